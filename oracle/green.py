@@ -1,0 +1,175 @@
+"""Green's functions of the oracle (plain FP64 NumPy/SciPy, test infrastructure).
+
+This module is test infrastructure: only ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import it.  It shares no code with
+the CUDA path.
+
+The paper solves lap(u) = f as u = G * f (Section "Methodology", eq. poisson)
+and defers the kernel formulas to its references (Section "Validation").  The
+readings used here, all pinned by the tests against the paper's printed
+convergence tables and against independent quadrature:
+
+* spectral (the singular kernel on fully spectral BCs):  G^ = -1/|k|^2, G^(0) = 0.
+* HEJ2m, regularised of order 2m: G = G0 * zeta_eps with a Gaussian-based
+  smoothing zeta whose transform is exp(-s) * sum_{j<m} s^j/j!,  s = |k|^2 eps^2/2,
+  eps = alpha*h (alpha = 2 by default).
+* LGF2 on spectral BCs: the inverse 7-point finite-difference symbol.
+* HEJ2 with d_u unbounded directions and spectral wavevector k_s (heat-kernel
+  form, a partial Fourier transform of the spectral HEJ2 kernel):
+
+      G(k_s, r) = - int_{eps^2/2}^inf exp(-t |k_s|^2) (4 pi t)^(-d_u/2) exp(-r^2/(4t)) dt
+
+  with the closed forms below for d_u = 3, for d_u = 1 and for k_s = 0.
+* HEJ0 (fully unbounded, spectral truncation of the kernel at |k| = pi/h):
+  G = -Si(pi r / h)/(2 pi^2 r),  G(0) = -1/(2 pi h).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import special
+
+SQRT2 = math.sqrt(2.0)
+EULER_GAMMA = 0.57721566490153286060651209008240243
+
+
+# ---------------------------------------------------------------------------
+# Fully spectral kernels, functions of the wavevector (Section "Validation",
+# symmetric and periodic case).  k2 = |k|^2; kdir = per-direction wavenumbers.
+# ---------------------------------------------------------------------------
+def spectral_kernel(name: str, k2: np.ndarray, eps: float, kdir=None, h=None) -> np.ndarray:
+    """G^(k) for fully spectral boundary conditions; the k = 0 mode is 0 (zero mean)."""
+    k2 = np.asarray(k2, dtype=np.float64)
+    out = np.zeros_like(k2)
+    nz = k2 > 0.0
+    if name == "spectral":
+        out[nz] = -1.0 / k2[nz]
+        return out
+    if name.startswith("hej") and name != "hej0":
+        m = int(name[3:]) // 2
+        s = k2[nz] * eps * eps / 2.0
+        acc = np.zeros_like(s)
+        term = np.ones_like(s)
+        for j in range(m):
+            if j > 0:
+                term = term * s / j
+            acc = acc + term
+        out[nz] = -np.exp(-s) * acc / k2[nz]
+        return out
+    if name == "lgf2":
+        # inverse of the 7-point Laplacian symbol: sum_d (2 - 2 cos(k_d h_d)) / h_d^2
+        sym = np.zeros_like(k2)
+        for kd, hd in zip(kdir, h):
+            sym = sym + (2.0 - 2.0 * np.cos(kd * hd)) / (hd * hd)
+        nzs = sym > 0.0
+        out = np.zeros_like(sym)
+        out[nzs] = -1.0 / sym[nzs]
+        return out
+    raise ValueError(f"kernel {name!r} has no fully spectral form in the oracle")
+
+
+# ---------------------------------------------------------------------------
+# Real-space and mixed HEJ2 kernels.
+# ---------------------------------------------------------------------------
+def hej2_3d(r: np.ndarray, eps: float) -> np.ndarray:
+    """d_u = 3: -erf(r/(sqrt2 eps))/(4 pi r), and -1/((2 pi)^{3/2} eps) at r = 0."""
+    r = np.asarray(r, dtype=np.float64)
+    out = np.full_like(r, -1.0 / ((2.0 * math.pi) ** 1.5 * eps))
+    nz = r > 0.0
+    out[nz] = -special.erf(r[nz] / (SQRT2 * eps)) / (4.0 * math.pi * r[nz])
+    return out
+
+
+def hej0_3d(r: np.ndarray, h: float) -> np.ndarray:
+    """Spectrally truncated kernel (cut-off pi/h): -Si(pi r/h)/(2 pi^2 r), -1/(2 pi h) at 0."""
+    r = np.asarray(r, dtype=np.float64)
+    out = np.full_like(r, -1.0 / (2.0 * math.pi * h))
+    nz = r > 0.0
+    si, _ = special.sici(math.pi * r[nz] / h)
+    out[nz] = -si / (2.0 * math.pi ** 2 * r[nz])
+    return out
+
+
+def hej2_1d(k: np.ndarray, z: np.ndarray, eps: float) -> np.ndarray:
+    """d_u = 1 (one unbounded direction, spectral wavenumber |k_s| = k).
+
+    k > 0: -(1/4k)[e^{-k|z|} erfc((k eps^2 - |z|)/(sqrt2 eps)) + e^{k|z|} erfc((k eps^2 + |z|)/(sqrt2 eps))]
+    k = 0: (|z|/2) erf(|z|/(sqrt2 eps)) + eps/sqrt(2 pi) exp(-z^2/(2 eps^2))   (1D Green |z|/2, smoothed)
+    The k > 0 form is evaluated with erfcx so that no exponential overflows.
+    """
+    k, z = np.broadcast_arrays(np.asarray(k, dtype=np.float64), np.abs(np.asarray(z, dtype=np.float64)))
+    out = np.empty(k.shape, dtype=np.float64)
+    zero = k == 0.0
+    zz = z[zero]
+    out[zero] = 0.5 * zz * special.erf(zz / (SQRT2 * eps)) + eps / math.sqrt(2.0 * math.pi) * np.exp(-zz * zz / (2.0 * eps * eps))
+    kk = k[~zero]
+    zz = z[~zero]
+    a = kk * eps / SQRT2
+    b = zz / (SQRT2 * eps)
+    gauss = np.exp(-a * a - b * b)
+    # e^{k|z|} erfc(a + b) = erfcx(a + b) exp(-a^2 - b^2)
+    t_plus = special.erfcx(a + b) * gauss
+    # e^{-k|z|} erfc(a - b): erfcx form when a >= b, direct form otherwise (no overflow either way)
+    amb = a - b
+    t_minus = np.where(amb >= 0.0, special.erfcx(np.maximum(amb, 0.0)) * gauss,
+                       np.exp(-kk * zz) * special.erfc(np.minimum(amb, 0.0)))
+    out[~zero] = -(t_minus + t_plus) / (4.0 * kk)
+    return out
+
+
+def _gauss_legendre(n: int):
+    x, w = np.polynomial.legendre.leggauss(n)
+    return x, w
+
+
+_GL_X, _GL_W = _gauss_legendre(24)
+
+
+def hej2_2d(k: np.ndarray, r: np.ndarray, eps: float) -> np.ndarray:
+    """d_u = 2 (two unbounded directions, spectral wavenumber |k_s| = k).
+
+    k = 0: (1/2pi)[ln r + E1(r^2/(2 eps^2))/2], and (ln(2 eps^2) - gamma)/(4 pi) at r = 0.
+    k > 0: the heat-kernel integral, with t = (eps^2/2) e^s:
+        G = -(1/4pi) int_0^inf exp(-a e^s - b e^{-s}) ds,  a = k^2 eps^2/2,  b = r^2/(2 eps^2),
+    by composite Gauss-Legendre on [0, s_max] where a e^{s_max} = 60.
+    """
+    k, r = np.broadcast_arrays(np.asarray(k, dtype=np.float64), np.asarray(r, dtype=np.float64))
+    out = np.empty(k.shape, dtype=np.float64)
+    zero = k == 0.0
+    rz = r[zero]
+    g0 = np.full(rz.shape, (math.log(2.0 * eps * eps) - EULER_GAMMA) / (4.0 * math.pi))
+    nzr = rz > 0.0
+    g0[nzr] = (np.log(rz[nzr]) + 0.5 * special.exp1(rz[nzr] ** 2 / (2.0 * eps * eps))) / (2.0 * math.pi)
+    out[zero] = g0
+
+    kk = k[~zero].ravel()
+    rr = r[~zero].ravel()
+    a = kk * kk * eps * eps / 2.0
+    b = rr * rr / (2.0 * eps * eps)
+    smax = np.log(np.maximum(60.0 / a, math.e))
+    npan = np.maximum(np.ceil(smax / 0.25).astype(np.int64), 1)
+    res = np.zeros_like(a)
+    # integrate panel by panel; points with fewer panels simply stop contributing
+    for p in range(int(npan.max()) if npan.size else 0):
+        live = npan > p
+        if not np.any(live):
+            break
+        width = smax[live] / npan[live]
+        lo = p * width
+        s = lo[:, None] + 0.5 * width[:, None] * (_GL_X[None, :] + 1.0)
+        f = np.exp(-a[live, None] * np.exp(s) - b[live, None] * np.exp(-s))
+        res[live] += 0.5 * width * (f @ _GL_W)
+    out[~zero] = (-res / (4.0 * math.pi)).reshape(kk.shape) if kk.size else res
+    return out
+
+
+def hej2_mixed(du: int, kmag: np.ndarray, r: np.ndarray, eps: float) -> np.ndarray:
+    """HEJ2 kernel with du unbounded directions, |k_s| = kmag and distance r."""
+    if du == 3:
+        return hej2_3d(r, eps)
+    if du == 2:
+        return hej2_2d(kmag, r, eps)
+    if du == 1:
+        return hej2_1d(kmag, r, eps)
+    raise ValueError("du must be 1, 2 or 3 here")
