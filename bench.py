@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""Throughput of the Fourier Poisson solve (FLUPS method) on GB300: one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+A step is one full solve (all passes of the hot path) of the workload's
+synthetic right-hand side, inputs resident in HBM.  Under torchrun (N > 1)
+every rank solves its own replica (weak scaling, no data-path collective).
+
+Default workload (`unb128_f64`): fully unbounded 3D Poisson, cell-centred
+128^3 FP64 (doubled to 256^3), unit cube, unit-mass Gaussian blob sigma = 0.1
+centred at 0.5 + seeded 1e-3 jitter, HEJ2 kernel eps = 2h.  Other workloads:
+per32_f64, unb128_f32, mixed257_f32, mixed257_f64, unb512_f32, per1024_f64.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2211_07777_gb300 import workloads as W  # noqa: E402
+
+L2_BYTES = 129 * 1024 * 1024
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz (1.26 TF)
+FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12  # 128 FP32 lanes/SM
+
+
+# ---------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------
+def workload(name):
+    """(description, n, bc, center, prec, kernel, rhs builder, L)."""
+    E, O, P, U = W.EVEN, W.ODD, W.PER, W.UNB
+    if name in ("unb128_f64", "unb128_f32", "unb512_f32"):
+        n = 512 if name == "unb512_f32" else 128
+        prec = 0 if name.endswith("f32") else 1
+        desc = f"fully unbounded {n}^3 cell-centred {'FP32' if prec == 0 else 'FP64'} (doubled {2*n}^3), " \
+               f"HEJ2 eps=2h, Gaussian blob sigma=0.1"
+        return dict(desc=desc, n=(n, n, n), bc=((U, U),) * 3, center=W.CELL, prec=prec, kernel="hej2",
+                    rhs=lambda: W.gaussian_blob((n, n, n), 0.1, W.blob_center(2)), L=(1.0, 1.0, 1.0))
+    if name in ("per32_f64", "per1024_f64"):
+        n = 32 if name == "per32_f64" else 1024
+        seed = 1 if n == 32 else 5
+        desc = f"fully periodic {n}^3 cell-centred FP64, spectral kernel, 4 seeded sine products"
+        return dict(desc=desc, n=(n, n, n), bc=((P, P),) * 3, center=W.CELL, prec=1, kernel="spectral",
+                    rhs=lambda: W.periodic_sines((n, n, n), W.sine_modes(seed)), L=(1.0, 1.0, 1.0))
+    if name in ("mixed257_f32", "mixed257_f64"):
+        prec = 0 if name.endswith("f32") else 1
+        desc = "node-centred 257x256x257, x even-even (DCT-I), y periodic, z unbounded, HEJ2, " \
+               f"{'FP32' if prec == 0 else 'FP64'}, Gaussian blob sigma=0.08 + 4 seeded y-modes"
+        return dict(desc=desc, n=(257, 256, 257), bc=((E, E), (P, P), (U, U)), center=W.NODE, prec=prec,
+                    kernel="hej2", rhs=lambda: W.mixed_blob_modes(), L=(1.0, 1.0, 1.0), h=(1 / 256,) * 3)
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ---------------------------------------------------------------------------
+# Clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# The oracle (CPU baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_problem(wl):
+    import oracle
+    n = wl["n"]
+    h = wl.get("h") or tuple(wl["L"][d] / (n[d] if wl["center"] == W.CELL else n[d] - 1) for d in range(3))
+    return oracle.Problem(bc=wl["bc"], h=tuple(h), center=wl["center"], kernel=wl["kernel"])
+
+
+def oracle_solve(wl, f):
+    import oracle
+    if wl["center"] == W.NODE and any(b[0] == W.PER for b in wl["bc"]):
+        # periodic node direction stored without its duplicate node: append it for the oracle
+        d = [i for i in range(3) if wl["bc"][i][0] == W.PER][0]
+        ax = 2 - d
+        full = np.concatenate([f, np.take(f, [0], axis=ax)], axis=ax)
+        out = oracle.solve(full, oracle_problem(wl))
+        return np.take(out, range(f.shape[ax]), axis=ax)
+    return oracle.solve(f, oracle_problem(wl))
+
+
+def cores_used():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def time_oracle(wl, f, budget_s=30.0, max_steps=None):
+    """Run the oracle repeatedly within a time budget; (seconds per solve, solves, result)."""
+    t0 = time.perf_counter()
+    ref = oracle_solve(wl, f)
+    times = [time.perf_counter() - t0]
+    while sum(times) + times[-1] < budget_s and (max_steps is None or len(times) < max_steps):
+        t0 = time.perf_counter()
+        oracle_solve(wl, f)
+        times.append(time.perf_counter() - t0)
+    return float(np.mean(times)), len(times), ref
+
+
+# ---------------------------------------------------------------------------
+def traffic_record(kernel_name, workload_name):
+    """ncu DRAM bytes per launch recorded under profiles/, if taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path)).get(f"{kernel_name}@{workload_name}")
+    except Exception:
+        return None
+    if not rec or rec.get("source_sha") != kernel_source_sha():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2211_07777_gb300", "csrc")
+    for fn in ("fft_engine.cuh", "passes.cuh", "passes.cu"):
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+KIND_NAMES = {0: "k_fwd_real", 1: "k_inv_real", 2: "k_fwd_c2c", 3: "k_inv_c2c", 4: "k_fused_real", 5: "k_fused_c2c"}
+
+
+def measured_peaks():
+    if os.path.exists(PEAKS_FILE):
+        try:
+            pk = json.load(open(PEAKS_FILE))
+            return float(pk["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM, "fallback"
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = workload(args.workload)
+    f = wl["rhs"]()
+    pts = float(np.prod(wl["n"]))
+    # warm-up: at most args.warmup solves within 60 s
+    t_end = time.perf_counter() + 60.0
+    for _ in range(max(0, args.warmup)):
+        oracle_solve(wl, f)
+        if time.perf_counter() > t_end:
+            break
+    # timed: the requested steps, bounded to about 150 s of CPU work
+    times = []
+    budget = 150.0
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        oracle_solve(wl, f)
+        times.append(time.perf_counter() - t0)
+        if sum(times) > budget:
+            break
+    sec = float(np.mean(times))
+    val = pts / sec / 1e6
+    line = {
+        "impl": "reference", "metric": "Mpts/s per Poisson solve", "value": val, "unit": "Mpts/s",
+        "n_gpus": args.gpus, "steps": len(times), "steps_requested": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "name": args.workload},
+        "cpu_baseline": {"value": val, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(times)} full oracle solve(s) of the workload (NumPy pocketfft, one thread)"},
+        "e2e": {"value": val, "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2211_07777_gb300 import flups as F
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = workload(args.workload)
+    prec = wl["prec"]
+    dt = torch.float32 if prec == 0 else torch.float64
+    f_host = wl["rhs"]()
+    pts = float(np.prod(wl["n"]))
+    solver = F.Solver(wl["n"], wl["bc"], L=wl["L"], center=wl["center"], prec=prec, green=wl["kernel"],
+                      h=wl.get("h"))
+    rhs = torch.from_numpy(f_host).to(dev, dt)
+    phi = torch.empty_like(rhs)
+    stream = torch.cuda.current_stream(dev)
+    npass = solver.info["launches"]
+    pinfo = [solver.pass_info(i) for i in range(npass)]
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    # parity check of this exact launch configuration against the oracle (rank 0, modest sizes only)
+    err = None
+    if rank == 0 and pts <= 2 ** 22:
+        solver.solve(phi, rhs, stream)
+        torch.cuda.synchronize()
+        ref = oracle_solve(wl, f_host)
+        err = float(np.abs(phi.double().cpu().numpy() - ref).max() / np.abs(ref).max())
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        solver.solve(phi, rhs, stream)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(npass + 1)] for _ in range(K)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        for k in range(K):
+            flush.zero_()            # L2 flush between timed solves (outside the per-step events)
+            for i in range(npass):
+                ev[k][i].record(stream)
+                solver.solve_pass(i, phi, rhs, stream)
+            ev[k][npass].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+        if K > 0 and t_wall < 1.5:
+            # keep sampling clocks under a comparable load for at least ~1.5 s (untimed)
+            t1 = time.perf_counter()
+            while time.perf_counter() - t1 < 1.5 - t_wall:
+                for _ in range(20):
+                    solver.solve(phi, rhs, stream)
+                torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    step_ms = [ev[k][0].elapsed_time(ev[k][npass]) for k in range(K)]
+    pass_ms = np.array([[ev[k][i].elapsed_time(ev[k][i + 1]) for i in range(npass)] for k in range(K)])
+    total_ms = float(np.sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / K
+    value = world * pts * K / (total_ms * 1e-3) / 1e6
+
+    # e2e: public API with pinned host buffers, H2D + solve + D2H every step
+    h_in = torch.from_numpy(f_host.astype(np.float32 if prec == 0 else np.float64)).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        solver.solve_host(h_out, h_in, stream)
+    Ke = max(3, min(K, 50))
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        solver.solve_host(h_out, h_in, stream)
+    e2e_s = (time.perf_counter() - t0) / Ke
+    e2e_val = world * pts / e2e_s / 1e6
+    nbytes = h_in.numel() * h_in.element_size()
+
+    # roofline of the dominant kernel
+    mean_pass = pass_ms.mean(axis=0)
+    dom = int(np.argmax(mean_pass))
+    kname = KIND_NAMES[pinfo[dom]["kind"]]
+    hbm, hbm_src = measured_peaks()
+    ach_gbs = pinfo[dom]["bytes"] / (mean_pass[dom] * 1e-3) / 1e9
+    ach_tf = pinfo[dom]["flops"] / (mean_pass[dom] * 1e-3) / 1e12
+    if prec == 1:
+        roof = {"bound": "alu", "achieved": ach_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach_tf / FP64_PEAK_TFLOPS,
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz",
+                "hbm_achieved_gbs": ach_gbs, "hbm_frac": ach_gbs / hbm, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src}
+    else:
+        roof = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm, "unit": "GB/s", "frac": ach_gbs / hbm,
+                "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else "fallback 6.8 TB/s"}
+    roof["kernel"] = kname
+    roof["traffic"] = traffic_record(kname, args.workload)
+    roof["algorithmic_bytes_per_launch"] = pinfo[dom]["bytes"]
+    roof["algorithmic_flops_per_launch"] = pinfo[dom]["flops"]
+    roof["launch_ms"] = float(mean_pass[dom])
+    model_bytes = sum(p["bytes"] for p in pinfo)
+    solve_frac = model_bytes / (ms_per_step * 1e-3) / 1e9 / hbm
+
+    line = {
+        "metric": "Mpts/s per Poisson solve", "value": value, "unit": "Mpts/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == 0 else "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "name": args.workload, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "max_rel_err_vs_oracle": err,
+        "passes": [{"kernel": KIND_NAMES[p["kind"]], "axis": p["axis"], "P": p["P"], "ms": float(m),
+                    "gbs": p["bytes"] / (m * 1e-3) / 1e9} for p, m in zip(pinfo, mean_pass)],
+        "solve_hbm_frac": solve_frac,
+        "roofline": roof,
+        "e2e": {"value": e2e_val, "unit": "Mpts/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": K * npass,
+        "clocks": clk.summary(),
+    }
+    # CPU baseline: the oracle on this host, rank 0, N = 1 only
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        if pts <= 2 ** 22:
+            sec, nsol, _ = time_oracle(wl, f_host, budget_s=20.0, max_steps=3)
+            line["cpu_baseline"] = {"value": pts / sec / 1e6, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"{nsol} full oracle solve(s) of the same workload "
+                                              f"(NumPy pocketfft, single thread)"}
+        else:
+            line["cpu_baseline"] = {"value": None, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
+                                    "sample": "skipped: the oracle's full extended box does not fit a bounded sample"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="unb128_f64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,150 @@
+/*
+ * flups_gpu.h -- C ABI of the GB300 Fourier Poisson solver (FLUPS method,
+ * arXiv 2211.07777).
+ *
+ * The library solves lap(phi) = f (Section "Methodology", eq. poisson) and the
+ * Biot-Savart variant lap(u) = curl(f) (Section "Application: the
+ * Biot-Savart solver", eq. biotsavart) on a uniform 3D grid, each face of
+ * each direction being periodic, even, odd or unbounded, with cell- or
+ * node-centred data (Section 2.1).  The solution is u = G * f computed as
+ * u^ = G^ f^ after a sequence of 1D transforms, one direction at a time.
+ *
+ * Conventions common to every entry point:
+ *   - Every function returns FLUPS_OK (0) on success or a negative
+ *     flups_status; none aborts, exits or throws across the ABI.
+ *   - Field arrays live in device memory, are contiguous and x-fastest: value
+ *     (i, j, k) is at i + n[0] * (j + n[1] * k).  A vector field (ncomp = 3)
+ *     is its 3 components back to back.  Element type: float (FLUPS_F32) or
+ *     double (FLUPS_F64), per the topology.
+ *   - Sizes per direction: N = L / h cells (given through h and L, must be
+ *     an integer).  Cell-centred data hold N values (x_j = (j + 1/2) h);
+ *     node-centred data hold N + 1 values (x_j = j h), except that a
+ *     node-centred periodic direction may also hold N values (the duplicate
+ *     f_N omitted).  N must be of the form 2^a 3^b with N >= 4; the
+ *     transform length (N, 2N or 4N per direction type) must not exceed 4096.
+ *   - Streams are `cudaStream_t` passed as `void*` (NULL = legacy default).
+ *   - Not thread safe per solver: one solver is used by one host thread and
+ *     one stream at a time.  Distinct solvers are independent.
+ */
+#ifndef FLUPS_GPU_H
+#define FLUPS_GPU_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum {
+  FLUPS_OK = 0,
+  FLUPS_EINVAL = -1,   /* null pointer, bad enum, bad argument value */
+  FLUPS_EBC = -2,      /* inadmissible boundary conditions (periodic on one face only, mismatched vector BCs) */
+  FLUPS_ESIZE = -3,    /* unsupported grid size (not 2^a 3^b, too large, too small) */
+  FLUPS_ENOMEM = -4,   /* device or host allocation failed */
+  FLUPS_ECUDA = -5,    /* a CUDA runtime call failed (see flups_last_cuda_error) */
+  FLUPS_EGREEN = -6,   /* Green kernel not available for these boundary conditions */
+  FLUPS_ESTATE = -7    /* call out of order (e.g. solve before setup) */
+} flups_status;
+
+/* Face conditions (Section 2.2, 2.3). */
+typedef enum { FLUPS_EVEN = 0, FLUPS_ODD = 1, FLUPS_PER = 3, FLUPS_UNB = 4 } flups_bc;
+/* Data layout (Section 2.1). */
+typedef enum { FLUPS_CELL = 0, FLUPS_NODE = 1 } flups_center;
+/* Arithmetic of the transforms. */
+typedef enum { FLUPS_F32 = 0, FLUPS_F64 = 1 } flups_prec;
+/* Operator. */
+typedef enum { FLUPS_POISSON = 0, FLUPS_BIOT_SAVART = 1 } flups_op;
+/* Green kernels (Section "Validation").  SPECTRAL is -1/|k|^2 with the zero
+ * mode set to 0 (spectral/periodic BCs only).  HEJ2..HEJ10: regularised of
+ * order 2m, eps = eps_over_h * max(h); HEJ4..HEJ10 on spectral BCs only.
+ * HEJ0: spectral truncation at pi/h, fully unbounded only.  LGF2: lattice
+ * Green's function, spectral BCs only. */
+typedef enum {
+  FLUPS_SPECTRAL = 0, FLUPS_HEJ0 = 1, FLUPS_HEJ2 = 2, FLUPS_HEJ4 = 4, FLUPS_HEJ6 = 6,
+  FLUPS_HEJ8 = 8, FLUPS_HEJ10 = 10, FLUPS_LGF2 = 100
+} flups_green;
+/* Derivative used in the spectral curl (Section "Application: the Biot-Savart solver"). */
+typedef enum { FLUPS_DIFF_SPECTRAL = 0, FLUPS_DIFF_FD2 = 2, FLUPS_DIFF_FD4 = 4, FLUPS_DIFF_FD6 = 6 } flups_diff;
+
+typedef struct flups_topo_s* flups_topo;
+typedef struct flups_solver_s* flups_solver;
+
+/* Grid topology.  n[3] = number of values per direction as stored by the
+ * caller (see the size conventions above); center = FLUPS_CELL/FLUPS_NODE;
+ * ncomp = 1 (scalar) or 3 (vector); prec = FLUPS_F32/FLUPS_F64.
+ * Host-only; allocates a small host object owned by the caller (free with
+ * flups_topo_free after the solvers built on it are cleaned up). */
+int flups_init_topo(const int n[3], int center, int ncomp, int prec, flups_topo* out);
+int flups_topo_free(flups_topo t);
+
+/* Solver.  bc = ncomp * 3 * 2 ints, [comp][dir][face], face 0 = left (x = 0),
+ * 1 = right (x = L); for FLUPS_POISSON with ncomp = 3 every component is
+ * solved independently with its own BCs.  For FLUPS_BIOT_SAVART (ncomp = 3)
+ * the BCs are those of the source f; the result u has in every direction the
+ * conditions of the curl (even and odd swapped along the differentiated
+ * direction).  h[3], L[3]: spacing and length per direction (h = L/N).
+ * green: flups_green.  eps_over_h: regularisation length in units of max(h)
+ * (2.0 in the paper's validation).  op: flups_op.  diff: flups_diff (ignored
+ * for FLUPS_POISSON).  Host-only; validates everything that does not need the
+ * device and returns FLUPS_EBC / FLUPS_ESIZE / FLUPS_EGREEN on violations. */
+int flups_init_solver(flups_topo t, const int* bc, const double h[3], const double L[3], int green,
+                      double eps_over_h, int op, int diff, flups_solver* out);
+
+/* Setup: plans the transforms (direction order by cost, Section 1),
+ * allocates the device workspace, builds twiddle tables (FP64, rounded once)
+ * and, with any unbounded direction, the Green's function spectrum (FP64 on
+ * the device, stored in the path precision).  Enqueued on `stream` and
+ * synchronised before returning.  *workspace_bytes (may be NULL) receives the
+ * device bytes the solver holds.  Calling it twice is a no-op. */
+int flups_setup(flups_solver s, void* stream, size_t* workspace_bytes);
+
+/* Solve: phi = G * rhs, both device arrays of the topology's shape (for the
+ * Biot-Savart operator, 3 components each).  phi == rhs is allowed (in
+ * place).  Enqueued on `stream`; returns without synchronising.  rhs is
+ * read-only unless phi == rhs. */
+int flups_solve(flups_solver s, void* phi, const void* rhs, void* stream);
+
+/* Same solve with HOST arrays: copies rhs host->device, solves, copies the
+ * result device->host, all on `stream`, and synchronises it.  Pinned host
+ * memory gives full copy bandwidth; pageable memory works. */
+int flups_solve_host(flups_solver s, void* phi_host, const void* rhs_host, void* stream);
+
+/* Releases the plan, the Green spectrum, the twiddles and the workspace.  The
+ * caller's arrays are never freed.  Safe on NULL. */
+int flups_cleanup(flups_solver s);
+
+/* Introspection (host-only, after flups_setup): number of kernel launches per
+ * solve; transform order (3 direction indices); algorithmic bytes moved per
+ * solve by the 5-pass model (each pass reads and writes its arrays once plus
+ * one read of the stored Green spectrum). */
+int flups_solver_info(flups_solver s, int* launches_per_solve, int order[3], double* model_bytes,
+                      double* green_bytes);
+
+/* Launch only pass i (0 <= i < launches_per_solve) of the solve on `stream`:
+ * the solve is exactly passes 0, 1, ... in order (pass 0 reads rhs, the last
+ * pass writes phi; the passes in between use the solver's workspace).  Lets a
+ * caller time each kernel with events on its own stream. */
+int flups_solve_pass(flups_solver s, int i, void* phi, const void* rhs, void* stream);
+/* Pass i: kernel kind (0 forward real, 1 inverse real, 2 forward C2C,
+ * 3 inverse C2C, 4 fused real, 5 fused C2C), transform axis, FFT length,
+ * algorithmic bytes (arrays read and written once, Green spectrum read once)
+ * and nominal flops (5 P log2 P per complex FFT of length P). */
+int flups_pass_info(flups_solver s, int i, int* kind, int* axis, int* fft_len, double* bytes, double* flops);
+
+/* Text of a status code (static storage). */
+const char* flups_strerror(int status);
+/* Text of the last CUDA error seen by the library in this process (static storage). */
+const char* flups_last_cuda_error(void);
+
+/* Test hook: evaluate the device FP64 special functions used by the Green's
+ * function generation at n points (device arrays x, y, out): which = 0 E1(x),
+ * 1 Si(x), 2 HEJ2 one-unbounded kernel G(k = x, z = y), 3 two-unbounded
+ * kernel G(k = x, r = y), 4 three-unbounded kernel G(r = y).  Synchronous. */
+int flups_debug_special(int which, const double* x, const double* y, double* out, int n, double eps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLUPS_GPU_H */

@@ -1,0 +1,739 @@
+// C ABI of the solver (include/flups_gpu.h): planner, device memory, launches.
+//
+// Planning follows Section 1 and Section "Methodology": each direction is
+// classified from its two face conditions into periodic, unbounded, one of
+// the four symmetric types of Table 1 or a semi-unbounded type (Section
+// 2.3.2); directions run in order of cost (symmetric, semi-unbounded,
+// periodic, unbounded); the first periodic/unbounded direction met on real
+// data is an R2C transform, later ones are C2C.  The last direction is fused:
+// forward transform, multiplication by G^ (eq. poisson), inverse transform.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "flups_gpu.h"
+#include "green.cuh"
+#include "passes.cuh"
+
+using namespace flups;
+
+namespace {
+
+thread_local std::string g_last_cuda = "no error";
+
+int cuda_fail(cudaError_t e, const char* where) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  g_last_cuda = buf;
+  return FLUPS_ECUDA;
+}
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e__ = (call);                      \
+    if (e__ != cudaSuccess) return cuda_fail(e__, #call); \
+  } while (0)
+
+bool is_2a3b(long n) {
+  if (n < 2) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+RadixPlan radix_plan(int P) {
+  RadixPlan rp{};
+  int p = P;
+  auto push = [&](int r) { rp.code |= (unsigned)r << (4 * rp.n); rp.n++; };
+  int a = 0;
+  while (p % 2 == 0) { ++a; p /= 2; }
+  // 2^a as 16s and one 8 or 4; a remainder of 2^1 is folded into 8 x 4
+  int n16 = a / 4, rem = a % 4;
+  if (rem == 1 && n16 > 0) { --n16; rem = 5; }
+  for (int i = 0; i < n16; ++i) push(0);  // nibble 0 encodes radix 16
+  if (rem == 5) { push(8); push(4); }
+  else if (rem == 3) push(8);
+  else if (rem == 2) push(4);
+  else if (rem == 1) push(2);
+  while (p % 3 == 0) { push(3); p /= 3; }
+  return rp;
+}
+
+// Direction type from its two faces (Section 1 categories, Table 1 parities).
+int classify(int l, int r, int* type) {
+  auto ok = [](int b) { return b == FLUPS_EVEN || b == FLUPS_ODD || b == FLUPS_PER || b == FLUPS_UNB; };
+  if (!ok(l) || !ok(r)) return FLUPS_EINVAL;
+  if (l == FLUPS_PER || r == FLUPS_PER) {
+    if (l != r) return FLUPS_EBC;
+    *type = T_PER;
+    return FLUPS_OK;
+  }
+  if (l == FLUPS_UNB && r == FLUPS_UNB) { *type = T_UNB; return FLUPS_OK; }
+  if (l == FLUPS_UNB) { *type = (r == FLUPS_EVEN) ? T_UE : T_UO; return FLUPS_OK; }
+  if (r == FLUPS_UNB) { *type = (l == FLUPS_EVEN) ? T_EU : T_OU; return FLUPS_OK; }
+  if (l == FLUPS_EVEN) *type = (r == FLUPS_EVEN) ? T_EE : T_EO;
+  else *type = (r == FLUPS_EVEN) ? T_OE : T_OO;
+  return FLUPS_OK;
+}
+
+int cost_class(int t) {
+  if (t >= T_EE && t <= T_OO) return 1;
+  if (t >= T_EU) return 2;
+  if (t == T_PER) return 3;
+  return 4;
+}
+
+bool is_quarter_t(int t) { return t == T_EO || t == T_OE; }
+bool is_semi_t(int t) { return t >= T_EU; }
+bool is_unb_like(int t) { return t == T_UNB || is_semi_t(t); }
+
+enum Role { R_R2R = 0, R_R2C = 1, R_C2C = 2 };
+
+struct DirPlan {
+  int type = 0, n_data = 0, N = 0, P = 0, role = 0, nm = 0, gext = 0, unb = 0;
+  double h = 0, L = 0, wscale = 0, wshift = 0;
+  RadixPlan rp{};
+  void* tw = nullptr;
+};
+
+struct Launch {
+  int kind;
+  PassParams p;
+  dim3 grid;
+  int nthr;
+  size_t smem;
+  int user_in, user_out;  // 1: the pointer is the caller's rhs / phi
+  double bytes, flops;    // algorithmic bytes moved and nominal FFT flops (5 P log2 P per complex FFT)
+};
+
+}  // namespace
+
+struct flups_topo_s {
+  int n[3];
+  int center, ncomp, prec;
+};
+
+struct flups_solver_s {
+  flups_topo_s topo;
+  int bc[3][3][2];
+  double h[3], L[3];
+  int green, op, diff;
+  double eps_over_h, eps;
+  int types[3];
+  DirPlan dir[3];
+  int order[3];
+  int dims[3][3];     // array dims after 0, 1, 2 forward passes
+  int cplx[3];        // element type of those arrays (0 real, 1 complex)
+  size_t elems1 = 0, elems2 = 0;
+  void* W1 = nullptr;
+  void* W2 = nullptr;
+  void* green_dev = nullptr;
+  void* tabs[3] = {nullptr, nullptr, nullptr};
+  void* stage = nullptr;  // device copy of the caller's host arrays (flups_solve_host)
+  size_t user_bytes = 0;
+  double green_bytes = 0, model_bytes = 0;
+  size_t ws_bytes = 0;
+  std::vector<Launch> passes;
+  bool ready = false;
+};
+
+namespace {
+
+size_t esize(int prec) { return prec == FLUPS_F32 ? 4 : 8; }
+
+// Twiddles exp(-2 pi i m/(2P)), m = 0..2P-1, in extended precision then rounded once.
+int make_twiddles(int P, int prec, void** out) {
+  const int M = 2 * P;
+  std::vector<double> re(M), im(M);
+  for (int m = 0; m < M; ++m) {
+    const long double a = 3.141592653589793238462643383279502884L * (long double)m / (long double)P;
+    re[m] = (double)cosl(a);
+    im[m] = (double)(-sinl(a));
+  }
+  const size_t bytes = (size_t)M * 2 * esize(prec);
+  void* d = nullptr;
+  CK(cudaMalloc(&d, bytes));
+  if (prec == FLUPS_F32) {
+    std::vector<float> h(2 * M);
+    for (int m = 0; m < M; ++m) { h[2 * m] = (float)re[m]; h[2 * m + 1] = (float)im[m]; }
+    CK(cudaMemcpy(d, h.data(), bytes, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<double> h(2 * M);
+    for (int m = 0; m < M; ++m) { h[2 * m] = re[m]; h[2 * m + 1] = im[m]; }
+    CK(cudaMemcpy(d, h.data(), bytes, cudaMemcpyHostToDevice));
+  }
+  *out = d;
+  return FLUPS_OK;
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5));
+    double pp = 0;
+    for (int it = 0; it < 100; ++it) {
+      double p1 = 1.0, p2 = 0.0;
+      for (int j = 1; j <= n; ++j) {
+        const double p3 = p2;
+        p2 = p1;
+        p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+      }
+      pp = n * (z * p1 - p2) / (z * z - 1.0);
+      const double z1 = z;
+      z = z1 - p1 / pp;
+      if (std::fabs(z - z1) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+  }
+}
+
+ArrDesc arr_desc(const int* d, int axis) {
+  ArrDesc a{};
+  const long long tot = (long long)d[0] * d[1] * d[2];
+  a.cs = tot;
+  if (axis == 0) { a.ls = d[0]; a.js = 1; a.os = 0; }
+  else if (axis == 1) { a.ls = 1; a.js = d[0]; a.os = (long long)d[0] * d[1]; }
+  else { a.ls = 1; a.js = (long long)d[0] * d[1]; a.os = d[0]; }
+  return a;
+}
+
+int ilog2(int w) { int l = 0; while ((1 << l) < w) ++l; return l; }
+
+// Tile shape: W lanes (power of 2) per CTA within a 2 x 32 KB ping-pong
+// shared-memory budget; about one radix-16 butterfly per thread and stage.
+void tile_shape(int P, int prec, int npen, bool packed, int* W, int* nthr) {
+  const int budget = prec == FLUPS_F32 ? 4096 : 2048;  // complex elements per buffer
+  int w = 1;
+  while (w * 2 * P <= budget && w < 64) w *= 2;
+  int need = packed ? (npen + 1) / 2 : npen;
+  int cap = 1;
+  while (cap < need) cap *= 2;
+  if (w > cap) w = cap;
+  if (w < 1) w = 1;
+  *W = w;
+  const int tmax = prec == FLUPS_F32 ? 512 : 256;
+  int t = (P * w + 15) / 16;
+  t = ((t + 31) / 32) * 32;
+  if (t < 64) t = 64;
+  if (t > tmax) t = tmax;
+  *nthr = t;
+}
+
+void fill_geom(Launch& L, const DirPlan& dp, int axis, const int* din, const int* dout, int prec, bool packed,
+               int center, int ncomp) {
+  PassParams& p = L.p;
+  p.ai = arr_desc(din, axis);
+  p.ao = arr_desc(dout, axis);
+  p.axis = axis;
+  p.npen = axis == 0 ? din[1] * din[2] : din[0];
+  int W, nthr;
+  tile_shape(dp.P, prec, p.npen, packed, &W, &nthr);
+  p.W = W;
+  p.lw = ilog2(W);
+  p.LS = (axis == 0 && W >= 8) ? W + 1 : W;
+  p.type = dp.type;
+  p.center = center;
+  p.N = dp.N;
+  p.n_data = dp.n_data;
+  p.P = dp.P;
+  p.n_modes = dp.nm;
+  p.n_use = (dp.type == T_PER) ? dp.N : dp.n_data;
+  p.plan = dp.rp;
+  p.tw = dp.tw;
+  const int per_tile = packed ? 2 * W : W;
+  L.grid = dim3((p.npen + per_tile - 1) / per_tile, axis == 0 ? 1 : (axis == 1 ? din[2] : din[1]), ncomp);
+  L.nthr = nthr;
+  L.smem = 2 * (size_t)dp.P * p.LS * 2 * esize(prec) + 16 * 2 * W + 16;
+}
+
+int setup_green(flups_solver_s* s, cudaStream_t st) {
+  const int prec = s->topo.prec;
+  int du = 0;
+  for (int d = 0; d < 3; ++d) du += s->dir[d].unb;
+  double Pprod = 1.0;
+  for (int d = 0; d < 3; ++d) Pprod *= s->dir[d].P;
+  if (du == 0) {
+    // closed form on the fly: per-direction |w|^2 (or the 7-point FD symbol for LGF2)
+    for (int d = 0; d < 3; ++d) {
+      const DirPlan& dp = s->dir[d];
+      std::vector<double> tab(dp.gext);
+      for (int g = 0; g < dp.gext; ++g) {
+        const double w = dp.wscale * (g + dp.wshift);
+        if (s->green == FLUPS_LGF2) {
+          const double sn = std::sin(0.5 * w * dp.h);
+          tab[g] = 4.0 * sn * sn / (dp.h * dp.h);
+        } else {
+          tab[g] = w * w;
+        }
+      }
+      const size_t bytes = dp.gext * esize(prec);
+      CK(cudaMalloc(&s->tabs[d], bytes));
+      if (prec == FLUPS_F32) {
+        std::vector<float> f(tab.begin(), tab.end());
+        CK(cudaMemcpy(s->tabs[d], f.data(), bytes, cudaMemcpyHostToDevice));
+      } else {
+        CK(cudaMemcpy(s->tabs[d], tab.data(), bytes, cudaMemcpyHostToDevice));
+      }
+      s->ws_bytes += bytes;
+    }
+    return FLUPS_OK;
+  }
+  // stored spectrum: sample G(k_s, r_u) in FP64, DCT-I along each unbounded-like direction
+  GreenSampleParams q{};
+  long long n = 1;
+  for (int d = 0; d < 3; ++d) {
+    const DirPlan& dp = s->dir[d];
+    q.gext[d] = dp.gext;
+    q.unb[d] = dp.unb;
+    q.h[d] = dp.h;
+    q.wscale[d] = dp.wscale;
+    q.wshift[d] = dp.wshift;
+    n *= dp.gext;
+  }
+  q.du = du;
+  q.kernel = s->green == FLUPS_HEJ0 ? 1 : 0;
+  q.eps = s->eps;
+  q.hmax = std::fmax(s->h[0], std::fmax(s->h[1], s->h[2]));
+  gauss_legendre(GL_N, q.gl_x, q.gl_w);
+  double* g64 = nullptr;
+  CK(cudaMalloc(&g64, n * sizeof(double)));
+  cudaError_t e = launch_green_sample(g64, q, st);
+  if (e) { cudaFree(g64); return cuda_fail(e, "green sample"); }
+  double vol = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    const DirPlan& dp = s->dir[d];
+    if (!dp.unb) continue;
+    vol *= dp.h;
+    // node-centred even-even forward pass on M+1 samples: the DCT-I of the symmetrised kernel
+    DirPlan gp{};
+    gp.type = T_EE;
+    gp.n_data = dp.gext;
+    gp.N = dp.gext - 1;
+    gp.P = 2 * gp.N;
+    gp.nm = dp.gext;
+    gp.rp = radix_plan(gp.P);
+    int rc = make_twiddles(gp.P, FLUPS_F64, &gp.tw);
+    if (rc) { cudaFree(g64); return rc; }
+    Launch L{};
+    L.kind = K_FWD_REAL;
+    fill_geom(L, gp, d, q.gext, q.gext, FLUPS_F64, true, FLUPS_NODE, 1);
+    L.p.in = g64;
+    L.p.out = g64;
+    e = launch_pass(L.kind, FLUPS_F64, L.p, L.grid, L.nthr, L.smem, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaFree(gp.tw);
+    if (e || e2) { cudaFree(g64); return cuda_fail(e ? e : e2, "green DCT-I"); }
+  }
+  const double scale = vol / Pprod;
+  const size_t bytes = n * esize(prec);
+  e = cudaMalloc(&s->green_dev, bytes);
+  if (e) { cudaFree(g64); return cuda_fail(e, "green alloc"); }
+  e = launch_green_finalize(g64, s->green_dev, prec, n, scale, st);
+  cudaError_t e2 = cudaStreamSynchronize(st);
+  cudaFree(g64);
+  if (e || e2) return cuda_fail(e ? e : e2, "green finalize");
+  s->green_bytes = (double)bytes;
+  s->ws_bytes += bytes;
+  return FLUPS_OK;
+}
+
+int build_plan(flups_solver_s* s) {
+  const int center = s->topo.center;
+  // per-direction geometry
+  for (int d = 0; d < 3; ++d) {
+    DirPlan& dp = s->dir[d];
+    dp.type = s->types[d];
+    dp.n_data = s->topo.n[d];
+    // N = L / h; the stored count must be N (cell), N + 1 (node), or N for a
+    // node-centred periodic direction given without its duplicate node
+    const double ratio = s->L[d] / s->h[d];
+    const long Nh = std::lround(ratio);
+    if (std::fabs(ratio - (double)Nh) > 1e-6 * ratio) return FLUPS_ESIZE;
+    if (center == FLUPS_CELL) {
+      if (dp.n_data != Nh) return FLUPS_ESIZE;
+    } else if (!(dp.n_data == Nh + 1 || (dp.type == T_PER && dp.n_data == Nh))) {
+      return FLUPS_ESIZE;
+    }
+    dp.N = (int)Nh;
+    if (!is_2a3b(dp.N) || dp.N < 4) return FLUPS_ESIZE;
+    const int t = dp.type;
+    dp.P = t == T_PER ? dp.N : ((t == T_UNB || t == T_EE || t == T_OO) ? 2 * dp.N : 4 * dp.N);
+    if (dp.P > 4096) return FLUPS_ESIZE;
+    dp.h = s->h[d];
+    dp.L = s->L[d];
+    dp.unb = is_unb_like(t);
+    if (t == T_PER) { dp.gext = dp.N / 2 + 1; dp.wscale = 2.0 * M_PI / dp.L; dp.wshift = 0.0; }
+    else if (t == T_UNB) { dp.gext = dp.N + 1; }
+    else if (is_semi_t(t)) { dp.gext = 2 * dp.N + 1; }
+    else if (is_quarter_t(t)) { dp.gext = dp.N; dp.wscale = M_PI / dp.L; dp.wshift = 0.5; }
+    else { dp.gext = dp.N + 1; dp.wscale = M_PI / dp.L; dp.wshift = 0.0; }
+    dp.rp = radix_plan(dp.P);
+  }
+  // order by cost, ties in x, y, z order
+  int ord[3] = {0, 1, 2};
+  for (int i = 0; i < 3; ++i)
+    for (int j = i + 1; j < 3; ++j)
+      if (cost_class(s->dir[ord[j]].type) < cost_class(s->dir[ord[i]].type) ||
+          (cost_class(s->dir[ord[j]].type) == cost_class(s->dir[ord[i]].type) && ord[j] < ord[i])) {
+        int tmp = ord[i]; ord[i] = ord[j]; ord[j] = tmp;
+      }
+  for (int i = 0; i < 3; ++i) s->order[i] = ord[i];
+  // roles and mode counts
+  bool real = true;
+  for (int i = 0; i < 3; ++i) {
+    DirPlan& dp = s->dir[ord[i]];
+    const int t = dp.type;
+    if (t == T_PER || t == T_UNB) {
+      if (real) { dp.role = R_R2C; dp.nm = dp.P / 2 + 1; real = false; }
+      else { dp.role = R_C2C; dp.nm = dp.P; }
+    } else {
+      dp.role = R_R2R;
+      dp.nm = is_semi_t(t) ? 2 * dp.N + 1 : (is_quarter_t(t) ? dp.N : dp.N + 1);
+    }
+  }
+  // array dims after each forward pass (the fused direction keeps its data size)
+  for (int d = 0; d < 3; ++d) s->dims[0][d] = s->topo.n[d];
+  s->cplx[0] = 0;
+  for (int i = 0; i < 2; ++i) {
+    const DirPlan& dp = s->dir[ord[i]];
+    for (int d = 0; d < 3; ++d) s->dims[i + 1][d] = s->dims[i][d];
+    s->dims[i + 1][ord[i]] = dp.nm;
+    s->cplx[i + 1] = s->cplx[i] || dp.role != R_R2R;
+  }
+  return FLUPS_OK;
+}
+
+int build_passes(flups_solver_s* s) {
+  const int prec = s->topo.prec, center = s->topo.center, nc = s->topo.ncomp;
+  const int* o = s->order;
+  const size_t es = esize(prec);
+  s->passes.clear();
+  double bytes = 0.0;
+  auto arr_bytes = [&](int i) {
+    const double n = (double)s->dims[i][0] * s->dims[i][1] * s->dims[i][2];
+    return n * es * (s->cplx[i] ? 2 : 1) * nc;
+  };
+  auto ffts = [&](const Launch& L, bool packed, int mult) {
+    const double P = L.p.P;
+    const double pencils = (double)L.p.npen * L.grid.y * nc;
+    const double n = packed ? std::ceil(pencils / 2.0) : pencils;
+    return mult * n * 5.0 * P * std::log2(P);
+  };
+  // 1: forward d1, user rhs -> W1
+  {
+    Launch L{};
+    L.kind = K_FWD_REAL;
+    fill_geom(L, s->dir[o[0]], o[0], s->dims[0], s->dims[1], prec, true, center, nc);
+    L.p.out = s->W1;
+    L.user_in = 1;
+    L.bytes = arr_bytes(0) + arr_bytes(1);
+    L.flops = ffts(L, true, 1);
+    s->passes.push_back(L);
+    bytes += L.bytes;
+  }
+  // 2: forward d2, W1 -> W2
+  {
+    Launch L{};
+    const bool real = !s->cplx[1];
+    L.kind = real ? K_FWD_REAL : K_FWD_C2C;
+    fill_geom(L, s->dir[o[1]], o[1], s->dims[1], s->dims[2], prec, real, center, nc);
+    L.p.in = s->W1;
+    L.p.out = s->W2;
+    L.bytes = arr_bytes(1) + arr_bytes(2);
+    L.flops = ffts(L, real, 1);
+    s->passes.push_back(L);
+    bytes += L.bytes;
+  }
+  // 3: fused d3 on W2, in place
+  {
+    Launch L{};
+    const bool real = !s->cplx[2];
+    L.kind = real ? K_FUSED_REAL : K_FUSED_C2C;
+    const DirPlan& dp = s->dir[o[2]];
+    fill_geom(L, dp, o[2], s->dims[2], s->dims[2], prec, real, center, nc);
+    L.p.in = s->W2;
+    L.p.out = s->W2;
+    FusedGreen& g = L.p.g;
+    g.stored = s->green_dev;
+    for (int d = 0; d < 3; ++d) {
+      g.tab[d] = s->tabs[d];
+      g.gext[d] = s->dir[d].gext;
+      g.fold[d] = (s->dir[d].role == R_C2C) ? s->dir[d].P : 0;
+    }
+    g.kernel = s->green;
+    g.eps2_half = 0.5 * s->eps * s->eps;
+    g.scale = 1.0 / ((double)s->dir[0].P * s->dir[1].P * s->dir[2].P);
+    g.quarter3 = is_quarter_t(dp.type);
+    g.dims1 = s->dims[2][1];
+    g.dims2 = s->dims[2][2];
+    L.bytes = 2 * arr_bytes(2) + s->green_bytes;
+    L.flops = ffts(L, real, 2);
+    s->passes.push_back(L);
+    bytes += L.bytes;
+  }
+  // 4: inverse d2, W2 -> W1
+  {
+    Launch L{};
+    const bool real = !s->cplx[1];
+    L.kind = real ? K_INV_REAL : K_INV_C2C;
+    fill_geom(L, s->dir[o[1]], o[1], s->dims[2], s->dims[1], prec, real, center, nc);
+    L.p.in = s->W2;
+    L.p.out = s->W1;
+    L.bytes = arr_bytes(1) + arr_bytes(2);
+    L.flops = ffts(L, real, 1);
+    s->passes.push_back(L);
+    bytes += L.bytes;
+  }
+  // 5: inverse d1, W1 -> user phi
+  {
+    Launch L{};
+    L.kind = K_INV_REAL;
+    fill_geom(L, s->dir[o[0]], o[0], s->dims[1], s->dims[0], prec, true, center, nc);
+    L.p.in = s->W1;
+    L.user_out = 1;
+    L.bytes = arr_bytes(0) + arr_bytes(1);
+    L.flops = ffts(L, true, 1);
+    s->passes.push_back(L);
+    bytes += L.bytes;
+  }
+  s->model_bytes = bytes;
+  for (const Launch& L : s->passes)
+    if (L.smem > 227 * 1024 || L.nthr > 1024) return FLUPS_ESIZE;
+  return FLUPS_OK;
+}
+
+std::once_flag g_limits_once;
+cudaError_t g_limits_err = cudaSuccess;
+
+}  // namespace
+
+extern "C" {
+
+const char* flups_strerror(int status) {
+  switch (status) {
+    case FLUPS_OK: return "ok";
+    case FLUPS_EINVAL: return "invalid argument";
+    case FLUPS_EBC: return "inadmissible boundary conditions";
+    case FLUPS_ESIZE: return "unsupported grid size";
+    case FLUPS_ENOMEM: return "out of memory";
+    case FLUPS_ECUDA: return "CUDA error";
+    case FLUPS_EGREEN: return "Green kernel not available for these boundary conditions";
+    case FLUPS_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* flups_last_cuda_error(void) { return g_last_cuda.c_str(); }
+
+int flups_init_topo(const int n[3], int center, int ncomp, int prec, flups_topo* out) {
+  if (!n || !out) return FLUPS_EINVAL;
+  if (center != FLUPS_CELL && center != FLUPS_NODE) return FLUPS_EINVAL;
+  if (ncomp != 1 && ncomp != 3) return FLUPS_EINVAL;
+  if (prec != FLUPS_F32 && prec != FLUPS_F64) return FLUPS_EINVAL;
+  for (int d = 0; d < 3; ++d)
+    if (n[d] < 2 || n[d] > 8193) return FLUPS_ESIZE;
+  flups_topo_s* t = new (std::nothrow) flups_topo_s;
+  if (!t) return FLUPS_ENOMEM;
+  for (int d = 0; d < 3; ++d) t->n[d] = n[d];
+  t->center = center;
+  t->ncomp = ncomp;
+  t->prec = prec;
+  *out = t;
+  return FLUPS_OK;
+}
+
+int flups_topo_free(flups_topo t) {
+  delete t;
+  return FLUPS_OK;
+}
+
+int flups_init_solver(flups_topo t, const int* bc, const double h[3], const double L[3], int green,
+                      double eps_over_h, int op, int diff, flups_solver* out) {
+  if (!t || !bc || !h || !L || !out) return FLUPS_EINVAL;
+  if (op != FLUPS_POISSON && op != FLUPS_BIOT_SAVART) return FLUPS_EINVAL;
+  if (op == FLUPS_BIOT_SAVART) return FLUPS_EINVAL;  // the curl path is added with its fused kernel
+  const int gk[] = {FLUPS_SPECTRAL, FLUPS_HEJ0, FLUPS_HEJ2, FLUPS_HEJ4, FLUPS_HEJ6, FLUPS_HEJ8, FLUPS_HEJ10, FLUPS_LGF2};
+  bool gok = false;
+  for (int g : gk) gok |= (g == green);
+  if (!gok) return FLUPS_EINVAL;
+  if (!(eps_over_h > 0.0)) return FLUPS_EINVAL;
+  for (int d = 0; d < 3; ++d)
+    if (!(h[d] > 0.0) || !(L[d] > 0.0)) return FLUPS_EINVAL;
+  flups_solver_s* s = new (std::nothrow) flups_solver_s;
+  if (!s) return FLUPS_ENOMEM;
+  s->topo = *t;
+  for (int c = 0; c < 3; ++c)
+    for (int d = 0; d < 3; ++d)
+      for (int f = 0; f < 2; ++f) s->bc[c][d][f] = c < t->ncomp ? bc[(c * 3 + d) * 2 + f] : bc[(d * 2) + f];
+  for (int d = 0; d < 3; ++d) {
+    s->h[d] = h[d];
+    s->L[d] = L[d];
+  }
+  s->green = green;
+  s->op = op;
+  s->diff = diff;
+  s->eps_over_h = eps_over_h;
+  s->eps = eps_over_h * std::fmax(h[0], std::fmax(h[1], h[2]));
+  int rc = FLUPS_OK;
+  for (int d = 0; d < 3 && rc == FLUPS_OK; ++d) rc = classify(s->bc[0][d][0], s->bc[0][d][1], &s->types[d]);
+  // a vector Poisson solve shares one plan: every component needs the same conditions
+  for (int c = 1; c < t->ncomp && rc == FLUPS_OK; ++c)
+    for (int d = 0; d < 3; ++d)
+      if (s->bc[c][d][0] != s->bc[0][d][0] || s->bc[c][d][1] != s->bc[0][d][1]) rc = FLUPS_EBC;
+  if (rc == FLUPS_OK) rc = build_plan(s);
+  if (rc == FLUPS_OK) {
+    int du = 0;
+    for (int d = 0; d < 3; ++d) du += s->dir[d].unb;
+    if (du == 0 && green == FLUPS_HEJ0) rc = FLUPS_EGREEN;
+    if (du > 0 && !(green == FLUPS_HEJ2 || (green == FLUPS_HEJ0 && du == 3))) rc = FLUPS_EGREEN;
+  }
+  if (rc != FLUPS_OK) {
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return FLUPS_OK;
+}
+
+int flups_setup(flups_solver s, void* stream, size_t* workspace_bytes) {
+  if (!s) return FLUPS_EINVAL;
+  if (s->ready) {
+    if (workspace_bytes) *workspace_bytes = s->ws_bytes;
+    return FLUPS_OK;
+  }
+  std::call_once(g_limits_once, [] { g_limits_err = set_pass_smem_limits(); });
+  if (g_limits_err) return cuda_fail(g_limits_err, "smem limits");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int prec = s->topo.prec, nc = s->topo.ncomp;
+  const size_t es = esize(prec);
+  for (int d = 0; d < 3; ++d) {
+    int rc = make_twiddles(s->dir[d].P, prec, &s->dir[d].tw);
+    if (rc) return rc;
+    s->ws_bytes += (size_t)4 * s->dir[d].P * es;
+  }
+  for (int i = 1; i <= 2; ++i) {
+    const size_t n = (size_t)s->dims[i][0] * s->dims[i][1] * s->dims[i][2] * nc * (s->cplx[i] ? 2 : 1);
+    void** buf = i == 1 ? &s->W1 : &s->W2;
+    cudaError_t e = cudaMalloc(buf, n * es);
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      return FLUPS_ENOMEM;
+    }
+    if (e) return cuda_fail(e, "workspace alloc");
+    s->ws_bytes += n * es;
+  }
+  int rc = setup_green(s, st);
+  if (rc) return rc;
+  rc = build_passes(s);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(st));
+  s->user_bytes = (size_t)s->topo.n[0] * s->topo.n[1] * s->topo.n[2] * nc * es;
+  s->ready = true;
+  if (workspace_bytes) *workspace_bytes = s->ws_bytes;
+  return FLUPS_OK;
+}
+
+int flups_solve(flups_solver s, void* phi, const void* rhs, void* stream) {
+  if (!s || !phi || !rhs) return FLUPS_EINVAL;
+  if (!s->ready) return FLUPS_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int prec = s->topo.prec;
+  for (Launch& L : s->passes) {
+    PassParams p = L.p;
+    if (L.user_in) p.in = rhs;
+    if (L.user_out) p.out = phi;
+    cudaError_t e = launch_pass(L.kind, prec, p, L.grid, L.nthr, L.smem, st);
+    if (e) return cuda_fail(e, "pass launch");
+  }
+  return FLUPS_OK;
+}
+
+int flups_solve_pass(flups_solver s, int i, void* phi, const void* rhs, void* stream) {
+  if (!s || !phi || !rhs) return FLUPS_EINVAL;
+  if (!s->ready) return FLUPS_ESTATE;
+  if (i < 0 || i >= (int)s->passes.size()) return FLUPS_EINVAL;
+  const Launch& L = s->passes[i];
+  PassParams p = L.p;
+  if (L.user_in) p.in = rhs;
+  if (L.user_out) p.out = phi;
+  cudaError_t e = launch_pass(L.kind, s->topo.prec, p, L.grid, L.nthr, L.smem, (cudaStream_t)stream);
+  if (e) return cuda_fail(e, "pass launch");
+  return FLUPS_OK;
+}
+
+int flups_pass_info(flups_solver s, int i, int* kind, int* axis, int* fft_len, double* bytes, double* flops) {
+  if (!s) return FLUPS_EINVAL;
+  if (!s->ready) return FLUPS_ESTATE;
+  if (i < 0 || i >= (int)s->passes.size()) return FLUPS_EINVAL;
+  const Launch& L = s->passes[i];
+  if (kind) *kind = L.kind;
+  if (axis) *axis = L.p.axis;
+  if (fft_len) *fft_len = L.p.P;
+  if (bytes) *bytes = L.bytes;
+  if (flops) *flops = L.flops;
+  return FLUPS_OK;
+}
+
+int flups_solve_host(flups_solver s, void* phi_host, const void* rhs_host, void* stream) {
+  if (!s || !phi_host || !rhs_host) return FLUPS_EINVAL;
+  if (!s->ready) return FLUPS_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!s->stage) {
+    cudaError_t e = cudaMalloc(&s->stage, s->user_bytes);
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      return FLUPS_ENOMEM;
+    }
+    if (e) return cuda_fail(e, "stage alloc");
+    s->ws_bytes += s->user_bytes;
+  }
+  CK(cudaMemcpyAsync(s->stage, rhs_host, s->user_bytes, cudaMemcpyHostToDevice, st));
+  int rc = flups_solve(s, s->stage, s->stage, stream);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(phi_host, s->stage, s->user_bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return FLUPS_OK;
+}
+
+int flups_cleanup(flups_solver s) {
+  if (!s) return FLUPS_OK;
+  for (int d = 0; d < 3; ++d) {
+    if (s->dir[d].tw) cudaFree(s->dir[d].tw);
+    if (s->tabs[d]) cudaFree(s->tabs[d]);
+  }
+  if (s->W1) cudaFree(s->W1);
+  if (s->W2) cudaFree(s->W2);
+  if (s->green_dev) cudaFree(s->green_dev);
+  if (s->stage) cudaFree(s->stage);
+  delete s;
+  return FLUPS_OK;
+}
+
+int flups_solver_info(flups_solver s, int* launches_per_solve, int order[3], double* model_bytes, double* green_bytes) {
+  if (!s) return FLUPS_EINVAL;
+  if (!s->ready) return FLUPS_ESTATE;
+  if (launches_per_solve) *launches_per_solve = (int)s->passes.size();
+  if (order)
+    for (int i = 0; i < 3; ++i) order[i] = s->order[i];
+  if (model_bytes) *model_bytes = s->model_bytes;
+  if (green_bytes) *green_bytes = s->green_bytes;
+  return FLUPS_OK;
+}
+
+int flups_debug_special(int which, const double* x, const double* y, double* out, int n, double eps) {
+  if (!x || !y || !out || n < 0) return FLUPS_EINVAL;
+  GreenSampleParams q{};
+  gauss_legendre(GL_N, q.gl_x, q.gl_w);
+  cudaError_t e = launch_special_eval(which, x, y, out, n, eps, q, 0);
+  if (e) return cuda_fail(e, "special eval");
+  CK(cudaDeviceSynchronize());
+  return FLUPS_OK;
+}
+
+}  // extern "C"

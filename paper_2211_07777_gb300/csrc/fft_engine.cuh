@@ -1,0 +1,209 @@
+// Shared-memory FFT engine for one tile of pencils (sm_103a).
+//
+// A tile holds W "lanes" of one complex sequence of length P each, laid out in
+// shared memory as S[j * LS + lane] (j = sequence index, LS >= W).  The
+// transform is a Stockham auto-sort FFT of P = 2^a 3^b in radix-16/8/4/2/3
+// stages; every stage reads its butterfly inputs from one shared buffer into
+// registers, applies the inter-stage twiddles and a register radix-R DFT, and
+// writes the outputs in natural order to the other buffer.  Twiddles
+// come from a table of exp(-2 pi i m / (2P)), m = 0 .. 2P-1, generated in FP64
+// on the host and rounded once to the path precision.
+//
+// The method's 1D transforms (Section "Methodology", eq. of Section 2.2: DFT,
+// DCT/DST I-IV through their periodic extensions) all reduce to this complex
+// FFT of the extended sequence.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace flups {
+
+template <typename T> struct cpx_t;
+template <> struct cpx_t<float> { using type = float2; };
+template <> struct cpx_t<double> { using type = double2; };
+template <typename T> using cpx = typename cpx_t<T>::type;
+
+template <typename T> __device__ __forceinline__ cpx<T> mk(T re, T im) { cpx<T> c; c.x = re; c.y = im; return c; }
+template <typename T> __device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename T> __device__ __forceinline__ cpx<T> cmulc(cpx<T> a, cpx<T> b) {
+  return mk<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename T> __device__ __forceinline__ cpx<T> cconj(cpx<T> a) { return mk<T>(a.x, -a.y); }
+template <typename T> __device__ __forceinline__ cpx<T> cscale(cpx<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <typename T, bool INV> __device__ __forceinline__ cpx<T> mul_mi(cpx<T> a) {
+  return INV ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+}
+
+// ---------------------------------------------------------------------------
+// Register DFTs of radix 2, 3, 4, 8, 16 (forward: exp(-2 pi i q r / R)).
+// The constants are the exact values cos(pi/4), cos(pi/8), sin(pi/8), sqrt(3)/2.
+// ---------------------------------------------------------------------------
+template <typename T, bool INV> __device__ __forceinline__ void dft2(cpx<T>& a, cpx<T>& b) {
+  cpx<T> t = a; a = cadd<T>(t, b); b = csub<T>(t, b);
+}
+
+template <typename T, bool INV> __device__ __forceinline__ void dft4(cpx<T>& a, cpx<T>& b, cpx<T>& c, cpx<T>& d) {
+  cpx<T> t0 = cadd<T>(a, c), t1 = csub<T>(a, c), t2 = cadd<T>(b, d), t3 = mul_mi<T, INV>(csub<T>(b, d));
+  a = cadd<T>(t0, t2); c = csub<T>(t0, t2); b = cadd<T>(t1, t3); d = csub<T>(t1, t3);
+}
+
+template <typename T, bool INV> __device__ __forceinline__ void dft3(cpx<T>& a, cpx<T>& b, cpx<T>& c) {
+  const T s3 = (T)0.86602540378443864676372317075294;
+  cpx<T> t1 = cadd<T>(b, c);
+  cpx<T> t2 = mk<T>(a.x - (T)0.5 * t1.x, a.y - (T)0.5 * t1.y);
+  cpx<T> t3 = mul_mi<T, INV>(cscale<T>(csub<T>(b, c), s3));
+  a = cadd<T>(a, t1); b = cadd<T>(t2, t3); c = csub<T>(t2, t3);
+}
+
+// rotate by W8^1 = (1 - i)/sqrt2 (forward) or its conjugate
+template <typename T, bool INV> __device__ __forceinline__ cpx<T> rot8_1(cpx<T> a) {
+  const T r = (T)0.70710678118654752440084436210485;
+  return INV ? mk<T>(r * (a.x - a.y), r * (a.x + a.y)) : mk<T>(r * (a.x + a.y), r * (a.y - a.x));
+}
+// rotate by W8^3 = (-1 - i)/sqrt2 (forward) or its conjugate
+template <typename T, bool INV> __device__ __forceinline__ cpx<T> rot8_3(cpx<T> a) {
+  const T r = (T)0.70710678118654752440084436210485;
+  return INV ? mk<T>(-r * (a.x + a.y), r * (a.x - a.y)) : mk<T>(r * (a.y - a.x), -r * (a.x + a.y));
+}
+
+template <typename T, bool INV> __device__ __forceinline__ void dft8(cpx<T>* v) {
+  // radix-2 DIT on top of two radix-4 DFTs
+  cpx<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  cpx<T> o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<T, INV>(e0, e1, e2, e3);
+  dft4<T, INV>(o0, o1, o2, o3);
+  o1 = rot8_1<T, INV>(o1);
+  o2 = mul_mi<T, INV>(o2);
+  o3 = rot8_3<T, INV>(o3);
+  v[0] = cadd<T>(e0, o0); v[4] = csub<T>(e0, o0);
+  v[1] = cadd<T>(e1, o1); v[5] = csub<T>(e1, o1);
+  v[2] = cadd<T>(e2, o2); v[6] = csub<T>(e2, o2);
+  v[3] = cadd<T>(e3, o3); v[7] = csub<T>(e3, o3);
+}
+
+template <typename T, bool INV> __device__ __forceinline__ cpx<T> tw16(cpx<T> a, int m) {
+  // multiply by W16^m, m in [0, 9]
+  const T c1 = (T)0.92387953251128675612818318939679;   // cos(pi/8)
+  const T s1 = (T)0.38268343236508977172845998403040;   // sin(pi/8)
+  const T r = (T)0.70710678118654752440084436210485;
+  T c, s;  // W16^m = c - i s (forward)
+  switch (m) {
+    case 0: return a;
+    case 1: c = c1; s = s1; break;
+    case 2: c = r; s = r; break;
+    case 3: c = s1; s = c1; break;
+    case 4: return mul_mi<T, INV>(a);
+    case 6: c = -r; s = r; break;
+    case 9: c = -c1; s = -s1; break;
+    default: c = (T)0; s = (T)0; break;
+  }
+  if (INV) s = -s;
+  return mk<T>(a.x * c + a.y * s, a.y * c - a.x * s);
+}
+
+template <typename T, bool INV> __device__ __forceinline__ void dft16(cpx<T>* v) {
+  // 4 x 4: columns n2 = 0..3 hold x[4 n1 + n2]
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<T, INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+  // now v[4 k1 + n2] = Y[n2][k1]; twiddle by W16^(n2 k1)
+  v[5] = tw16<T, INV>(v[5], 1);
+  v[6] = tw16<T, INV>(v[6], 2);
+  v[7] = tw16<T, INV>(v[7], 3);
+  v[9] = tw16<T, INV>(v[9], 2);
+  v[10] = tw16<T, INV>(v[10], 4);
+  v[11] = tw16<T, INV>(v[11], 6);
+  v[13] = tw16<T, INV>(v[13], 3);
+  v[14] = tw16<T, INV>(v[14], 6);
+  v[15] = tw16<T, INV>(v[15], 9);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<T, INV>(v[4 * k1 + 0], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+  // v[4 k1 + k2] = X[k1 + 4 k2]: transpose the 4 x 4 index
+  cpx<T> t[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) t[i] = v[i];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
+}
+
+template <typename T, int R, bool INV> __device__ __forceinline__ void dftR(cpx<T>* v) {
+  if constexpr (R == 2) dft2<T, INV>(v[0], v[1]);
+  else if constexpr (R == 3) dft3<T, INV>(v[0], v[1], v[2]);
+  else if constexpr (R == 4) dft4<T, INV>(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 8) dft8<T, INV>(v);
+  else if constexpr (R == 16) dft16<T, INV>(v);
+}
+
+// ---------------------------------------------------------------------------
+// One Stockham stage over the whole tile, from buffer X to buffer Y (ping-pong:
+// no thread has to hold more than one butterfly, whatever the tile size).
+// ---------------------------------------------------------------------------
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void stage(const cpx<T>* X, cpx<T>* Y, int LS, int P, int W, int lw, int Ns,
+                                      const cpx<T>* __restrict__ tw, int tid, int nthr) {
+  const int nbf = P / R;
+  const int total = nbf * W;
+  const int tstride = (2 * P) / (Ns * R);
+  for (int idx = tid; idx < total; idx += nthr) {
+    const int lane = idx & (W - 1);
+    const int j = idx >> lw;
+    const int k = j % Ns;
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = X[(j + r * nbf) * LS + lane];
+    if (Ns > 1) {
+      const int step = tstride * k;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const cpx<T> w = __ldg(&tw[r * step]);
+        v[r] = INV ? cmulc<T>(v[r], w) : cmul<T>(v[r], w);
+      }
+    }
+    dftR<T, R, INV>(v);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) Y[(base + r * Ns) * LS + lane] = v[r];
+  }
+}
+
+// Radix plan: up to 8 stages, radices in {16, 8, 4, 2, 3}, one radix per
+// 4-bit nibble of `code` (stage s: (code >> 4s) & 15, where 0 stands for 16),
+// so that the plan is read without indexing an array of the kernel parameters.
+struct RadixPlan {
+  int n;
+  unsigned code;
+};
+
+// Transform the tile held in A (B is scratch of the same size); returns the
+// buffer that holds the result.  Ends with a block barrier.
+template <typename T, bool INV>
+__device__ __forceinline__ cpx<T>* fft_tile(cpx<T>* A, cpx<T>* B, int LS, int P, int W, int lw, const RadixPlan& plan,
+                                            const cpx<T>* __restrict__ tw, int tid, int nthr) {
+  int Ns = 1;
+  cpx<T>* X = A;
+  cpx<T>* Y = B;
+  for (int s = 0; s < plan.n; ++s) {
+    const int nib = (int)((plan.code >> (4 * s)) & 15u);
+    switch (nib) {
+      case 0: stage<T, 16, INV>(X, Y, LS, P, W, lw, Ns, tw, tid, nthr); Ns *= 16; break;
+      case 8: stage<T, 8, INV>(X, Y, LS, P, W, lw, Ns, tw, tid, nthr); Ns *= 8; break;
+      case 4: stage<T, 4, INV>(X, Y, LS, P, W, lw, Ns, tw, tid, nthr); Ns *= 4; break;
+      case 3: stage<T, 3, INV>(X, Y, LS, P, W, lw, Ns, tw, tid, nthr); Ns *= 3; break;
+      default: stage<T, 2, INV>(X, Y, LS, P, W, lw, Ns, tw, tid, nthr); Ns *= 2; break;
+    }
+    __syncthreads();
+    cpx<T>* t = X;
+    X = Y;
+    Y = t;
+  }
+  return X;
+}
+
+}  // namespace flups

@@ -1,0 +1,234 @@
+// Green's function spectrum generation, FP64 on the device.
+//
+// The solve needs G^ = FFT of the Green's function on the extended domain
+// (Section 2.3.1: G sampled on the doubled domain and symmetrised about L;
+// Section 2.3.2: evaluated on the padded domain of a semi-unbounded direction
+// and cosine-transformed).  For a symmetrised G the doubled-domain DFT is a
+// type-I DCT of the samples G(m h), m = 0..M, so every unbounded-like
+// direction is handled by one node-centred even-even forward pass on FP64
+// data.  Spectral directions enter through their wavenumber: with d_u
+// unbounded directions and spectral wavevector k_s the regularised kernel is
+//     G(k_s, r) = - int_{eps^2/2}^inf exp(-t |k_s|^2) (4 pi t)^(-d_u/2) exp(-r^2/(4t)) dt,
+// a partial Fourier transform of the fully spectral HEJ2 kernel
+// -exp(-|k|^2 eps^2/2)/|k|^2 (Section "Validation": kernels HEJ2..HEJ10,
+// HEJ0, LGF2, CHAT2).  Closed forms:
+//   d_u = 3: -erf(r/(sqrt2 eps))/(4 pi r),    G(0) = -1/((2 pi)^{3/2} eps)
+//   d_u = 1: k > 0: -(1/4k)[e^{-k z} erfc((k eps^2 - z)/(sqrt2 eps)) + e^{k z} erfc((k eps^2 + z)/(sqrt2 eps))]
+//            k = 0: (z/2) erf(z/(sqrt2 eps)) + eps/sqrt(2 pi) e^{-z^2/(2 eps^2)}
+//   d_u = 2: k = 0: (1/2pi)[ln r + E1(r^2/(2 eps^2))/2],  G(0) = (ln(2 eps^2) - gamma)/(4 pi)
+//            k > 0: composite Gauss-Legendre quadrature of the integral in s = ln(2t/eps^2)
+// and the spectrally truncated HEJ0 kernel (cut-off pi/h, d_u = 3):
+//   -Si(pi r/h)/(2 pi^2 r),  G(0) = -1/(2 pi h).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "green.cuh"
+
+namespace flups {
+
+#define PI_D 3.14159265358979323846264338327950288
+#define EULER_D 0.57721566490153286060651209008240243
+
+// E1(x) for x > 0: power series for x <= 1, continued fraction (modified
+// Lentz) of exp(x) E1(x) = 1/(x+1- 1/(x+3- 4/(x+5- ...))) otherwise.
+__device__ double expint_e1(double x) {
+  if (x <= 1.0) {
+    double sum = 0.0, term = 1.0;
+    for (int k = 1; k < 40; ++k) {
+      term *= -x / k;
+      const double add = term / k;
+      sum += add;
+      if (fabs(add) < 1e-18 * fabs(sum)) break;
+    }
+    return -EULER_D - log(x) - sum;
+  }
+  const double tiny = 1e-300;
+  double b = x + 1.0, c = 1.0 / tiny, d = 1.0 / b, h = d;
+  for (int i = 1; i < 500; ++i) {
+    const double a = -(double)i * i;
+    b += 2.0;
+    d = 1.0 / (a * d + b);
+    c = b + a / c;
+    const double del = c * d;
+    h *= del;
+    if (fabs(del - 1.0) < 1e-16) break;
+  }
+  return h * exp(-x);
+}
+
+// Si(x), x >= 0: series for x <= 4, otherwise pi/2 + Im E1(i x) through the
+// complex continued fraction of E1(z) at z = i x, since E1(ix) = -Ci(x) + i(Si(x) - pi/2).
+__device__ double sine_integral(double x) {
+  if (x <= 4.0) {
+    const double x2 = x * x;
+    double term = x, sum = x;
+    for (int k = 1; k < 60; ++k) {
+      term *= -x2 / ((2.0 * k) * (2.0 * k + 1.0));
+      const double add = term / (2.0 * k + 1.0);
+      sum += add;
+      if (fabs(add) < 1e-18 * fabs(sum)) break;
+    }
+    return sum;
+  }
+  // Lentz on the complex fraction 1/(z+1- 1/(z+3- 4/(z+5- ...))), z = i x
+  double br = 1.0, bi = x;                 // b = z + 1
+  double cr = 1e300, ci = 0.0;             // c = 1/tiny
+  double den = br * br + bi * bi;
+  double dr = br / den, di = -bi / den;    // d = 1/b
+  double hr = dr, hi = di;
+  for (int i = 1; i < 1000; ++i) {
+    const double a = -(double)i * i;
+    br += 2.0;
+    // d = 1/(a d + b)
+    double tr = a * dr + br, ti = a * di + bi;
+    den = tr * tr + ti * ti;
+    dr = tr / den;
+    di = -ti / den;
+    // c = b + a/c
+    den = cr * cr + ci * ci;
+    cr = br + a * cr / den;
+    ci = bi - a * ci / den;
+    const double delr = cr * dr - ci * di, deli = cr * di + ci * dr;
+    const double nr = hr * delr - hi * deli, ni = hr * deli + hi * delr;
+    hr = nr;
+    hi = ni;
+    if (fabs(delr - 1.0) + fabs(deli) < 1e-16) break;
+  }
+  // E1(ix) = exp(-ix) h
+  double s, c;
+  sincos(x, &s, &c);
+  const double e1i = -s * hr + c * hi;     // Im(exp(-ix) h) = Im((c - i s)(hr + i hi))
+  return 0.5 * PI_D + e1i;                 // Si = pi/2 + Im E1(ix)
+}
+
+__device__ double hej2_du3(double r, double eps) {
+  if (r == 0.0) return -1.0 / (pow(2.0 * PI_D, 1.5) * eps);
+  return -erf(r / (sqrt(2.0) * eps)) / (4.0 * PI_D * r);
+}
+
+__device__ double hej0_du3(double r, double h) {
+  if (r == 0.0) return -1.0 / (2.0 * PI_D * h);
+  return -sine_integral(PI_D * r / h) / (2.0 * PI_D * PI_D * r);
+}
+
+__device__ double hej2_du1(double k, double z, double eps) {
+  z = fabs(z);
+  const double s2 = sqrt(2.0);
+  if (k == 0.0) return 0.5 * z * erf(z / (s2 * eps)) + eps / sqrt(2.0 * PI_D) * exp(-z * z / (2.0 * eps * eps));
+  const double a = k * eps / s2, b = z / (s2 * eps);
+  const double gauss = exp(-a * a - b * b);
+  const double tplus = erfcx(a + b) * gauss;
+  const double amb = a - b;
+  const double tminus = amb >= 0.0 ? erfcx(amb) * gauss : exp(-k * z) * erfc(amb);
+  return -(tminus + tplus) / (4.0 * k);
+}
+
+__device__ double hej2_du2(double k, double r, double eps, const GreenSampleParams& q) {
+  if (k == 0.0) {
+    if (r == 0.0) return (log(2.0 * eps * eps) - EULER_D) / (4.0 * PI_D);
+    return (log(r) + 0.5 * expint_e1(r * r / (2.0 * eps * eps))) / (2.0 * PI_D);
+  }
+  // -(1/4pi) int_0^inf exp(-a e^s - b e^-s) ds over the range where the exponent is below 50
+  const double a = 0.5 * k * k * eps * eps, b = r * r / (2.0 * eps * eps);
+  double lo, hi;
+  if (b > 0.0) {
+    const double c = sqrt(a * b);
+    if (2.0 * c > 50.0) return 0.0;
+    const double sstar = 0.5 * log(b / a);
+    const double del = acosh(25.0 / c);
+    lo = fmax(0.0, sstar - del);
+    hi = sstar + del;
+    if (hi <= lo) return 0.0;
+  } else {
+    if (a >= 50.0) return 0.0;
+    lo = 0.0;
+    hi = log(50.0 / a);
+  }
+  const int npan = max(1, (int)ceil((hi - lo) / 0.25));
+  const double w = (hi - lo) / npan;
+  double acc = 0.0;
+  for (int pn = 0; pn < npan; ++pn) {
+    const double mid = lo + (pn + 0.5) * w;
+    double pacc = 0.0;
+    for (int j = 0; j < GL_N; ++j) {
+      const double s = mid + 0.5 * w * q.gl_x[j];
+      pacc += q.gl_w[j] * exp(-a * exp(s) - b * exp(-s));
+    }
+    acc += 0.5 * w * pacc;
+  }
+  return -acc / (4.0 * PI_D);
+}
+
+__global__ void k_green_sample(double* __restrict__ g, GreenSampleParams q) {
+  const long long tot = (long long)q.gext[0] * q.gext[1] * q.gext[2];
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int gi[3];
+    gi[0] = (int)(idx % q.gext[0]);
+    const long long rest = idx / q.gext[0];
+    gi[1] = (int)(rest % q.gext[1]);
+    gi[2] = (int)(rest / q.gext[1]);
+    double k2 = 0.0, r2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      if (q.unb[d]) {
+        const double r = gi[d] * q.h[d];
+        r2 += r * r;
+      } else {
+        const double w = q.wscale[d] * (gi[d] + q.wshift[d]);
+        k2 += w * w;
+      }
+    }
+    const double k = sqrt(k2), r = sqrt(r2);
+    double v;
+    if (q.kernel == 1) v = hej0_du3(r, q.hmax);
+    else if (q.du == 3) v = hej2_du3(r, q.eps);
+    else if (q.du == 2) v = hej2_du2(k, r, q.eps, q);
+    else v = hej2_du1(k, r, q.eps);
+    g[idx] = v;
+  }
+}
+
+template <typename T>
+__global__ void k_green_finalize(const double* __restrict__ g, T* __restrict__ out, long long n, double scale) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (T)(g[i] * scale);
+}
+
+cudaError_t launch_green_sample(double* g, const GreenSampleParams& q, cudaStream_t st) {
+  const long long tot = (long long)q.gext[0] * q.gext[1] * q.gext[2];
+  long long blocks = (tot + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_green_sample<<<(unsigned)blocks, 256, 0, st>>>(g, q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_green_finalize(const double* g, void* out, int prec, long long n, double scale, cudaStream_t st) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (prec == 0) k_green_finalize<float><<<(unsigned)blocks, 256, 0, st>>>(g, (float*)out, n, scale);
+  else k_green_finalize<double><<<(unsigned)blocks, 256, 0, st>>>(g, (double*)out, n, scale);
+  return cudaGetLastError();
+}
+
+// Device-side special functions exposed for tests through a small evaluation kernel.
+__global__ void k_special_eval(int which, const double* __restrict__ x, const double* __restrict__ y, double* out, int n,
+                               double eps, GreenSampleParams q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  switch (which) {
+    case 0: out[i] = expint_e1(x[i]); break;
+    case 1: out[i] = sine_integral(x[i]); break;
+    case 2: out[i] = hej2_du1(x[i], y[i], eps); break;
+    case 3: out[i] = hej2_du2(x[i], y[i], eps, q); break;
+    case 4: out[i] = hej2_du3(y[i], eps); break;
+    default: out[i] = 0.0; break;
+  }
+}
+
+cudaError_t launch_special_eval(int which, const double* x, const double* y, double* out, int n, double eps,
+                                const GreenSampleParams& q, cudaStream_t st) {
+  k_special_eval<<<(n + 127) / 128, 128, 0, st>>>(which, x, y, out, n, eps, q);
+  return cudaGetLastError();
+}
+
+}  // namespace flups

@@ -1,0 +1,28 @@
+// Green's function spectrum generation (FP64), see green.cu.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace flups {
+
+constexpr int GL_N = 16;  // Gauss-Legendre nodes per quadrature panel
+
+struct GreenSampleParams {
+  int gext[3];        // Green index extents (x, y, z)
+  int unb[3];         // 1: unbounded-like direction (sampled at r = g h), 0: spectral
+  double h[3];        // grid spacing per direction
+  double wscale[3];   // spectral wavenumber w = wscale (g + wshift)
+  double wshift[3];
+  int du;             // number of unbounded-like directions
+  int kernel;         // 0 HEJ2, 1 HEJ0
+  double eps;         // regularisation length
+  double hmax;        // HEJ0 cut-off spacing
+  double gl_x[GL_N];  // Gauss-Legendre nodes and weights on [-1, 1]
+  double gl_w[GL_N];
+};
+
+cudaError_t launch_green_sample(double* g, const GreenSampleParams& q, cudaStream_t st);
+cudaError_t launch_green_finalize(const double* g, void* out, int prec, long long n, double scale, cudaStream_t st);
+cudaError_t launch_special_eval(int which, const double* x, const double* y, double* out, int n, double eps,
+                                const GreenSampleParams& q, cudaStream_t st);
+
+}  // namespace flups

@@ -1,0 +1,65 @@
+// Pass descriptors shared by the host planner and the pass kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_engine.cuh"
+
+namespace flups {
+
+// Per-direction transform type (Section "Methodology": 4 categories; the
+// symmetric ones split by face parity, Table 1; semi-unbounded by side).
+enum DirType : int {
+  T_PER = 0, T_UNB = 1,
+  T_EE = 2, T_EO = 3, T_OE = 4, T_OO = 5,
+  T_EU = 6, T_OU = 7, T_UE = 8, T_UO = 9,
+};
+enum Center : int { C_CELL = 0, C_NODE = 1 };
+
+__host__ __device__ inline bool is_quarter(int t) { return t == T_EO || t == T_OE; }
+__host__ __device__ inline bool is_semi(int t) { return t >= T_EU; }
+__host__ __device__ inline bool is_reversed(int t) { return t == T_UE || t == T_UO; }
+// coefficient taken from the real part (even at the origin face) or minus the imaginary part
+__host__ __device__ inline bool is_odd_origin(int t) { return t == T_OO || t == T_OE || t == T_OU || t == T_UO; }
+
+// Element addressing of an array seen as pencils along the pass axis:
+// offset = q * ls + j * js + o * os + comp * cs, q = pencil position along the
+// lane dimension (x for axis 1/2, the row y + ny z for axis 0), j = index along
+// the axis, o = the remaining coordinate (blockIdx.y), comp = vector component.
+struct ArrDesc {
+  long long ls, js, os, cs;
+};
+
+// Green's function access in the fused pass.
+struct FusedGreen {
+  const void* stored;     // stored real spectrum (path precision) or nullptr for closed form
+  const void* tab[3];     // closed form: per-direction |w|^2 (or FD symbol) tables, path precision
+  int gext[3];            // Green index extents (x, y, z)
+  int fold[3];            // green index = fold ? min(i, fold - i) : i, for the two non-axis dirs
+  int kernel;             // closed-form kernel id (0 spectral, 2..10 HEJ order, 100 LGF2)
+  double eps2_half;       // eps^2 / 2
+  double scale;           // 1 / (P1 P2 P3) (closed form only; the stored spectrum is pre-scaled)
+  int quarter3;           // the fused direction is a quarter-wave type
+  int dims1, dims2;       // for axis-0 passes: y extent of the array (row -> (y, z))
+};
+
+struct PassParams {
+  const void* in;
+  void* out;
+  ArrDesc ai, ao;
+  int axis;
+  int npen;               // pencils along the lane dimension
+  int W, lw, LS;          // lanes per tile (power of 2), log2, smem lane stride
+  int type, center, N, n_data, P, n_modes;
+  int n_use;              // data values used (node periodic: N)
+  RadixPlan plan;
+  const void* tw;         // exp(-2 pi i m/(2P)), m < 2P, path precision
+  FusedGreen g;
+};
+
+// host launchers (passes.cu)
+enum PassKind : int { K_FWD_REAL = 0, K_INV_REAL = 1, K_FWD_C2C = 2, K_INV_C2C = 3, K_FUSED_REAL = 4, K_FUSED_C2C = 5 };
+cudaError_t launch_pass(int kind, int prec, const PassParams& p, dim3 grid, int nthreads, size_t smem, cudaStream_t st);
+cudaError_t set_pass_smem_limits();
+
+}  // namespace flups

@@ -1,0 +1,232 @@
+"""Python binding of the C ABI in include/flups_gpu.h (argument marshalling only).
+
+Every function of the header is exposed under the same name; each raises
+FlupsError on a non-zero status.  Device arrays are passed as torch CUDA
+tensors (or raw integer device pointers); streams as torch.cuda.Stream or raw
+handles.  The library is loaded from this package directory; if it is absent
+the first call raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libflups_gpu.so")
+
+EVEN, ODD, PER, UNB = 0, 1, 3, 4
+CELL, NODE = 0, 1
+F32, F64 = 0, 1
+POISSON, BIOT_SAVART = 0, 1
+SPECTRAL, HEJ0, HEJ2, HEJ4, HEJ6, HEJ8, HEJ10, LGF2 = 0, 1, 2, 4, 6, 8, 10, 100
+DIFF_SPECTRAL, DIFF_FD2, DIFF_FD4, DIFF_FD6 = 0, 2, 4, 6
+KERNELS = {"spectral": SPECTRAL, "hej0": HEJ0, "hej2": HEJ2, "hej4": HEJ4, "hej6": HEJ6, "hej8": HEJ8,
+           "hej10": HEJ10, "lgf2": LGF2}
+
+EXPORTED = (
+    "flups_init_topo", "flups_topo_free", "flups_init_solver", "flups_setup", "flups_solve",
+    "flups_solve_host", "flups_cleanup", "flups_solver_info", "flups_strerror", "flups_last_cuda_error",
+    "flups_debug_special", "flups_solve_pass", "flups_pass_info",
+)
+
+
+class FlupsError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = f"{where}: {_strerror(status)} ({status})"
+        if status == -5:
+            msg += f" [{lib().flups_last_cuda_error().decode()}]"
+        super().__init__(msg)
+        self.status = status
+
+
+_LIB = None
+
+
+def lib():
+    """The loaded C library (raises if the CUDA extension has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA extension missing: {LIB_PATH} (run paper_2211_07777_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+        L.flups_init_topo.argtypes = [ip, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
+        L.flups_topo_free.argtypes = [vp]
+        L.flups_init_solver.argtypes = [vp, ip, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(vp)]
+        L.flups_setup.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.flups_solve.argtypes = [vp, vp, vp, vp]
+        L.flups_solve_host.argtypes = [vp, vp, vp, vp]
+        L.flups_cleanup.argtypes = [vp]
+        L.flups_solver_info.argtypes = [vp, ip, ip, dp, dp]
+        L.flups_strerror.argtypes = [ctypes.c_int]
+        L.flups_strerror.restype = ctypes.c_char_p
+        L.flups_last_cuda_error.restype = ctypes.c_char_p
+        L.flups_debug_special.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int, ctypes.c_double]
+        L.flups_solve_pass.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+        L.flups_pass_info.argtypes = [vp, ctypes.c_int, ip, ip, ip, dp, dp]
+        for name in EXPORTED:
+            if name not in ("flups_strerror", "flups_last_cuda_error"):
+                getattr(L, name).restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def _strerror(status: int) -> str:
+    return lib().flups_strerror(int(status)).decode()
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise FlupsError(status, where)
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(s) -> int:
+    if s is None:
+        return 0
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# --- the C ABI, one function each -------------------------------------------------
+def flups_init_topo(n, center, ncomp, prec):
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_int * 3)(*[int(v) for v in n])
+    _check(lib().flups_init_topo(arr, int(center), int(ncomp), int(prec), ctypes.byref(h)), "flups_init_topo")
+    return h
+
+
+def flups_topo_free(topo):
+    _check(lib().flups_topo_free(topo), "flups_topo_free")
+
+
+def flups_init_solver(topo, bc, h, L, green, eps_over_h=2.0, op=POISSON, diff=DIFF_SPECTRAL):
+    """bc: [comp][dir][face] nested sequence (ncomp x 3 x 2) or [dir][face] for one component."""
+    flat = []
+    if isinstance(bc[0][0], (list, tuple)):
+        for comp in bc:
+            for d in comp:
+                flat.extend(int(b) for b in d)
+    else:
+        for d in bc:
+            flat.extend(int(b) for b in d)
+    arr = (ctypes.c_int * len(flat))(*flat)
+    hh = (ctypes.c_double * 3)(*[float(v) for v in h])
+    LL = (ctypes.c_double * 3)(*[float(v) for v in L])
+    g = KERNELS[green] if isinstance(green, str) else int(green)
+    s = ctypes.c_void_p()
+    _check(lib().flups_init_solver(topo, arr, hh, LL, g, float(eps_over_h), int(op), int(diff), ctypes.byref(s)),
+           "flups_init_solver")
+    return s
+
+
+def flups_setup(solver, stream=None) -> int:
+    ws = ctypes.c_size_t(0)
+    _check(lib().flups_setup(solver, _stream(stream), ctypes.byref(ws)), "flups_setup")
+    return ws.value
+
+
+def flups_solve(solver, phi, rhs, stream=None):
+    _check(lib().flups_solve(solver, _ptr(phi), _ptr(rhs), _stream(stream)), "flups_solve")
+
+
+def flups_solve_host(solver, phi_host, rhs_host, stream=None):
+    _check(lib().flups_solve_host(solver, _ptr(phi_host), _ptr(rhs_host), _stream(stream)), "flups_solve_host")
+
+
+def flups_cleanup(solver):
+    _check(lib().flups_cleanup(solver), "flups_cleanup")
+
+
+def flups_solver_info(solver):
+    n = ctypes.c_int(0)
+    order = (ctypes.c_int * 3)()
+    mb = ctypes.c_double(0)
+    gb = ctypes.c_double(0)
+    _check(lib().flups_solver_info(solver, ctypes.byref(n), order, ctypes.byref(mb), ctypes.byref(gb)),
+           "flups_solver_info")
+    return {"launches": n.value, "order": list(order), "model_bytes": mb.value, "green_bytes": gb.value}
+
+
+def flups_solve_pass(solver, i, phi, rhs, stream=None):
+    _check(lib().flups_solve_pass(solver, int(i), _ptr(phi), _ptr(rhs), _stream(stream)), "flups_solve_pass")
+
+
+def flups_pass_info(solver, i):
+    kind, axis, P = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    b, fl = ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib().flups_pass_info(solver, int(i), ctypes.byref(kind), ctypes.byref(axis), ctypes.byref(P),
+                                 ctypes.byref(b), ctypes.byref(fl)), "flups_pass_info")
+    return {"kind": kind.value, "axis": axis.value, "P": P.value, "bytes": b.value, "flops": fl.value}
+
+
+def flups_debug_special(which, x, y, out, n, eps):
+    _check(lib().flups_debug_special(int(which), _ptr(x), _ptr(y), _ptr(out), int(n), float(eps)),
+           "flups_debug_special")
+
+
+# --- convenience wrapper ------------------------------------------------------------
+class Solver:
+    """One planned solve: Solver(n, bc, h=..., ...) then solve(phi, rhs) on CUDA tensors."""
+
+    def __init__(self, n, bc, L=(1.0, 1.0, 1.0), center=CELL, prec=F64, green="spectral", eps_over_h=2.0,
+                 op=POISSON, diff=DIFF_SPECTRAL, ncomp=None, h=None, stream=None):
+        if ncomp is None:
+            ncomp = 3 if op == BIOT_SAVART else 1
+        self.n = tuple(int(v) for v in n)
+        self.ncomp = ncomp
+        self.prec = prec
+        if h is None:
+            # N = n (cell) or n - 1 (node); a node-centred periodic direction stored
+            # without its duplicate node needs h given explicitly (h = L / n)
+            h = [L[d] / (self.n[d] if center == CELL else self.n[d] - 1) for d in range(3)]
+        self.h = tuple(h)
+        self._topo = flups_init_topo(self.n, center, ncomp, prec)
+        try:
+            self._s = flups_init_solver(self._topo, bc, self.h, L, green, eps_over_h, op, diff)
+        except Exception:
+            flups_topo_free(self._topo)
+            self._topo = None
+            raise
+        self.workspace_bytes = flups_setup(self._s, stream)
+        self.info = flups_solver_info(self._s)
+
+    def solve(self, phi, rhs, stream=None):
+        flups_solve(self._s, phi, rhs, stream)
+
+    def solve_pass(self, i, phi, rhs, stream=None):
+        flups_solve_pass(self._s, i, phi, rhs, stream)
+
+    def pass_info(self, i):
+        return flups_pass_info(self._s, i)
+
+    def solve_host(self, phi_host, rhs_host, stream=None):
+        flups_solve_host(self._s, phi_host, rhs_host, stream)
+
+    def close(self):
+        if getattr(self, "_s", None) is not None:
+            flups_cleanup(self._s)
+            self._s = None
+        if getattr(self, "_topo", None) is not None:
+            flups_topo_free(self._topo)
+            self._topo = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -1,0 +1,176 @@
+"""CUDA path against the oracle, element by element, through the C ABI.
+
+Tolerances (relative L_inf, max|phi - phi_ref| / max|phi_ref|): FP64 1e-12,
+FP32 1e-5 -- the bounds stated for the method's two arithmetic paths, both far
+below the discretisation errors they must not mask (1e-2 .. 1e-6 here).
+"""
+import json
+import math
+import os
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import CELL, NODE, EVEN as E, ODD as O, PER, UNB as U
+from paper_2211_07777_gb300 import flups as F
+from tests import analytic
+from tests.gpu_util import cuda_solve, rel_linf
+
+pytestmark = pytest.mark.gpu
+
+TOL = {F.F64: 1e-12, F.F32: 1e-5}
+TYPES = {"PER": (PER, PER), "UNB": (U, U), "EE": (E, E), "EO": (E, O), "OE": (O, E), "OO": (O, O),
+         "EU": (E, U), "OU": (O, U), "UE": (U, E), "UO": (U, O)}
+
+
+def _sweep():
+    """Every direction type on every axis, the other two axes drawn with a fixed seed."""
+    rng = np.random.default_rng(2211)
+    names = list(TYPES)
+    out = []
+    for ax in range(3):
+        for t in names:
+            others = list(rng.choice(names, size=2))
+            combo = []
+            for d in range(3):
+                combo.append(t if d == ax else others.pop(0))
+            out.append(tuple(combo))
+    return out
+
+
+CASES = _sweep()
+_ORACLE_CACHE = {}
+
+
+def _kernel(types):
+    return "hej2" if any("U" in t for t in types) else "spectral"
+
+
+def _oracle(types, center, shape, seed):
+    key = (types, center, shape, seed)
+    if key not in _ORACLE_CACHE:
+        rng = np.random.default_rng(seed)
+        f = rng.standard_normal(shape)
+        n = (shape[2], shape[1], shape[0])
+        h = tuple(1.0 / (n[d] if center == CELL else n[d] - 1) for d in range(3))
+        prob = oracle.Problem(bc=tuple(TYPES[t] for t in types), h=h, center=center, kernel=_kernel(types))
+        _ORACLE_CACHE[key] = (f, oracle.solve(f, prob))
+    return _ORACLE_CACHE[key]
+
+
+@pytest.mark.parametrize("prec", [F.F64, F.F32], ids=["f64", "f32"])
+@pytest.mark.parametrize("center", [CELL, NODE], ids=["cell", "node"])
+@pytest.mark.parametrize("types", CASES, ids=["-".join(c) for c in CASES])
+def test_bc_sweep_matches_oracle(types, center, prec):
+    shape = (8, 12, 16) if center == CELL else (9, 13, 17)  # [z, y, x]: x 16 cells, y 12, z 8
+    f, ref = _oracle(types, center, shape, seed=zlib.crc32("-".join(types).encode()) % 1000)
+    bc = tuple(TYPES[t] for t in types)
+    out, _ = cuda_solve(f, bc, center, prec, _kernel(types))
+    assert rel_linf(out, ref) < TOL[prec], rel_linf(out, ref)
+
+
+@pytest.mark.parametrize("types,shape", [
+    (("UNB", "UNB", "UNB"), (24, 36, 48)),
+    (("PER", "PER", "PER"), (27, 48, 96)),
+    (("EE", "PER", "UNB"), (18, 32, 24)),
+    (("OO", "EO", "PER"), (32, 24, 18)),
+], ids=["unb", "per", "ee-per-unb", "oo-eo-per"])
+@pytest.mark.parametrize("prec", [F.F64, F.F32], ids=["f64", "f32"])
+def test_several_tiles_and_ragged_tails(types, shape, prec):
+    f, ref = _oracle(types, CELL, shape, seed=7)
+    out, _ = cuda_solve(f, tuple(TYPES[t] for t in types), CELL, prec, _kernel(types))
+    assert rel_linf(out, ref) < TOL[prec]
+
+
+def test_in_place_solve():
+    types = ("EE", "PER", "UNB")
+    f, ref = _oracle(types, CELL, (8, 12, 16), seed=3)
+    out, _ = cuda_solve(f, tuple(TYPES[t] for t in types), CELL, F.F64, "hej2", in_place=True)
+    assert rel_linf(out, ref) < 1e-12
+
+
+def test_node_periodic_without_duplicate_point():
+    """Node-centred periodic direction given as N values (f_N omitted)."""
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal((17, 16, 17))        # z node UNB 16 cells, y periodic N = 16 (no duplicate), x EE
+    full = np.concatenate([f, f[:, :1, :]], axis=1)   # the same field with the duplicate node
+    h = 1.0 / 16
+    prob = oracle.Problem(bc=((E, E), (PER, PER), (U, U)), h=(h, h, h), center=NODE, kernel="hej2")
+    ref = oracle.solve(full, prob)[:, :16, :]
+    out, _ = cuda_solve(f, ((E, E), (PER, PER), (U, U)), NODE, F.F64, "hej2", h=(h, h, h))
+    assert rel_linf(out, ref) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# The paper's printed E_inf through the CUDA path.
+# ---------------------------------------------------------------------------
+with open(os.path.join(os.path.dirname(__file__), "golden", "paper_einf.json")) as fh:
+    _G = json.load(fh)
+
+
+@pytest.mark.parametrize("kernel", ["spectral", "lgf2", "hej2", "hej4", "hej6", "hej8", "hej10"])
+def test_printed_symmetric_periodic_on_gpu(kernel):
+    N = 32
+    phi, f = analytic.case_symmetric_periodic(N)
+    out, _ = cuda_solve(f, ((E, E), (O, E), (PER, PER)), NODE, F.F64, kernel)
+    err = np.abs(out - phi).max()
+    want = _G["symmetric_periodic"][kernel]["33"]
+    if want < 1e-13:
+        assert err < 5e-15
+    else:
+        assert abs(err - want) < 1e-10 * want
+
+
+@pytest.mark.parametrize("kernel", ["hej2", "hej0"])
+def test_printed_unbounded_on_gpu(kernel):
+    N = 32
+    phi, f = analytic.case_unbounded(N)
+    out, _ = cuda_solve(f, ((U, U),) * 3, NODE, F.F64, kernel)
+    err = np.abs(out - phi).max()
+    want = _G["unbounded"][kernel]["33"]
+    assert abs(err - want) < (1e-10 if kernel == "hej2" else 1e-7) * want
+
+
+def test_printed_semi_unbounded_on_gpu():
+    N = 32
+    phi, f = analytic.case_semi_unbounded(N)
+    out, _ = cuda_solve(f, ((U, E), (U, U), (O, U)), NODE, F.F64, "hej2")
+    err = np.abs(out - phi).max()
+    assert abs(err - _G["semi_unbounded"]["hej2"]["33"]) < 1e-10 * _G["semi_unbounded"]["hej2"]["33"]
+
+
+# ---------------------------------------------------------------------------
+# Device special functions against SciPy.
+# ---------------------------------------------------------------------------
+def test_device_special_functions():
+    import torch
+    from scipy import special
+    eps = 0.05
+    x = np.concatenate([np.linspace(1e-3, 1.0, 50), np.linspace(1.0, 60.0, 200), [1e-8, 0.5, 700.0]])
+    y = np.linspace(0.0, 1.2, x.size)
+    X = torch.tensor(x, device="cuda", dtype=torch.float64)
+    Y = torch.tensor(y, device="cuda", dtype=torch.float64)
+    out = torch.empty_like(X)
+    F.flups_debug_special(0, X, Y, out, x.size, eps)
+    np.testing.assert_allclose(out.cpu().numpy(), special.exp1(x), rtol=2e-14, atol=0)
+    xs = np.concatenate([np.linspace(0.0, 4.0, 50), np.linspace(4.0, 3000.0, 400)])
+    Xs = torch.tensor(xs, device="cuda", dtype=torch.float64)
+    Ys = torch.zeros_like(Xs)
+    out = torch.empty_like(Xs)
+    F.flups_debug_special(1, Xs, Ys, out, xs.size, eps)
+    np.testing.assert_allclose(out.cpu().numpy(), special.sici(xs)[0], rtol=1e-14, atol=1e-15)
+    k = np.concatenate([[0.0, 0.0, 0.0], np.geomspace(1e-3, 800.0, 60)])
+    z = np.concatenate([[0.0, 0.3, 1.7], np.linspace(0.0, 1.5, 60)])
+    K = torch.tensor(k, device="cuda", dtype=torch.float64)
+    Z = torch.tensor(z, device="cuda", dtype=torch.float64)
+    out = torch.empty_like(K)
+    F.flups_debug_special(2, K, Z, out, k.size, eps)
+    ref = oracle.green.hej2_1d(k, z, eps)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-13, atol=1e-300)
+    F.flups_debug_special(3, K, Z, out, k.size, eps)
+    ref = oracle.green.hej2_2d(k, z, eps)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-12, atol=1e-17)
+    F.flups_debug_special(4, K, Z, out, k.size, eps)
+    np.testing.assert_allclose(out.cpu().numpy(), oracle.green.hej2_3d(z, eps), rtol=1e-14)
