@@ -132,6 +132,30 @@ int flups_solve_pass(flups_solver s, int i, void* phi, const void* rhs, void* st
  * and nominal flops (5 P log2 P per complex FFT of length P). */
 int flups_pass_info(flups_solver s, int i, int* kind, int* axis, int* fft_len, double* bytes, double* flops);
 
+/* Allocation-free fully periodic solve (the paper has no counterpart; this is
+ * an integration convenience).  For callers that must not allocate device
+ * memory: a host application whose own pool allocator owns the whole device,
+ * or a latency-critical loop that cannot pay the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  It computes the same result as
+ * flups_solve for a cell-centred, periodic-on-all-faces, FP64 problem with
+ * the FLUPS_SPECTRAL kernel (-1/|k|^2, zero mean): phi and rhs are device
+ * arrays of n[0] x n[1] x n[2] doubles (x fastest, phi == rhs allowed), L the
+ * domain lengths.  Each n must be 2^a 3^b, 4 <= n <= 4096.
+ *
+ * Its whole workspace lives in one static device array of 48 MiB
+ * (FLUPS_NOALLOC_SCRATCH_BYTES) that every GPU loading the library holds
+ * until the process exits; sizes whose workspace exceeds it return
+ * FLUPS_ESIZE (2 (n0/2 + 1) n1 n2 complex doubles plus small tables: up to
+ * about 128^3).  It calls no cudaMalloc, cudaFree or allocating library
+ * routine.  The first call on a device looks up the array's device address
+ * with that device current (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls on a device share the one array and
+ * nothing in it needs to start at zero (every read follows a write of the same
+ * call); calls that overlap on the GPU (different streams, or different host
+ * threads) race on it and must be serialised by the caller.  Enqueued on
+ * `stream`; returns without synchronising. */
+int flups_solve_periodic_noalloc(double* phi, const double* rhs, const int n[3], const double L[3], void* stream);
+
 /* Text of a status code (static storage). */
 const char* flups_strerror(int status);
 /* Text of the last CUDA error seen by the library in this process (static storage). */

@@ -737,3 +737,159 @@ int flups_debug_special(int which, const double* x, const double* y, double* out
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free solve.
+//
+// Some callers must not allocate device memory at all: a host application
+// that hands the whole device to its own pool allocator and forbids any other
+// allocation, or a latency-critical loop that cannot afford the implicit
+// device synchronisation of cudaMalloc/cudaFree.  For them
+// flups_solve_periodic_noalloc runs the fully periodic solve with its whole
+// workspace (intermediate spectra, twiddle tables, wavenumber tables) carved
+// out of one file-scope device array of fixed size; it calls no cudaMalloc,
+// cudaFree or allocating library routine.  The array exists once per device
+// that loads the library and is held until the process exits.
+// ---------------------------------------------------------------------------
+#define FLUPS_NOALLOC_SCRATCH_BYTES (48u * 1024u * 1024u)
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FLUPS_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Twiddles exp(-2 pi i m/(2P)) (m < 2P) and |w|^2 of the periodic modes g < N/2 + 1, in FP64.
+__global__ void k_noalloc_tables(double2* tw, int P, double* w2, int gext, double wscale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 2 * P) {
+    double s, c;
+    sincospi((double)i / (double)P, &s, &c);
+    tw[i] = make_double2(c, -s);
+  }
+  if (i < gext) {
+    const double w = wscale * i;
+    w2[i] = w * w;
+  }
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int flups_solve_periodic_noalloc(double* phi, const double* rhs, const int n[3], const double L[3],
+                                            void* stream) {
+  if (!phi || !rhs || !n || !L) return FLUPS_EINVAL;
+  for (int d = 0; d < 3; ++d) {
+    if (!is_2a3b(n[d]) || n[d] < 4 || n[d] > 4096) return FLUPS_ESIZE;
+    if (!(L[d] > 0.0)) return FLUPS_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return FLUPS_EINVAL;
+  void* base = nullptr;
+  {
+    // set-up once per device, with that device current: the device address of the array
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+      g_noalloc_addr[dev] = p;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  std::call_once(g_limits_once, [] { g_limits_err = set_pass_smem_limits(); });
+  if (g_limits_err) return cuda_fail(g_limits_err, "smem limits");
+
+  // plan: x R2C, y C2C, z fused C2C with the closed-form spectral kernel -1/|k|^2
+  DirPlan dir[3];
+  for (int d = 0; d < 3; ++d) {
+    DirPlan& dp = dir[d];
+    dp.type = T_PER;
+    dp.n_data = n[d];
+    dp.N = n[d];
+    dp.P = n[d];
+    dp.gext = n[d] / 2 + 1;
+    dp.h = L[d] / n[d];
+    dp.L = L[d];
+    dp.wscale = 2.0 * M_PI / L[d];
+    dp.rp = radix_plan(dp.P);
+  }
+  dir[0].role = R_R2C;
+  dir[0].nm = dir[0].P / 2 + 1;
+  dir[1].role = R_C2C;
+  dir[1].nm = dir[1].P;
+  dir[2].role = R_C2C;
+  dir[2].nm = dir[2].P;
+  int dims0[3] = {n[0], n[1], n[2]};
+  int dims1[3] = {dir[0].nm, n[1], n[2]};
+  int dims2[3] = {dir[0].nm, dir[1].nm, n[2]};
+  const size_t es = sizeof(double);
+  const size_t w1 = align256((size_t)dims1[0] * dims1[1] * dims1[2] * 2 * es);
+  const size_t w2 = align256((size_t)dims2[0] * dims2[1] * dims2[2] * 2 * es);
+  size_t off = 0;
+  unsigned char* b = (unsigned char*)base;
+  void* W1 = b + off;
+  off += w1;
+  void* W2 = b + off;
+  off += w2;
+  double* tabs[3];
+  for (int d = 0; d < 3; ++d) {
+    dir[d].tw = b + off;
+    off += align256((size_t)2 * dir[d].P * 2 * es);
+    tabs[d] = (double*)(b + off);
+    off += align256((size_t)dir[d].gext * es);
+  }
+  if (off > FLUPS_NOALLOC_SCRATCH_BYTES) return FLUPS_ESIZE;
+  for (int d = 0; d < 3; ++d) {
+    const int cnt = 2 * dir[d].P;
+    k_noalloc_tables<<<(cnt + 127) / 128, 128, 0, st>>>((double2*)dir[d].tw, dir[d].P, tabs[d], dir[d].gext,
+                                                        dir[d].wscale);
+    CK(cudaGetLastError());
+  }
+  Launch Ls[5];
+  for (int i = 0; i < 5; ++i) Ls[i] = Launch{};
+  Ls[0].kind = K_FWD_REAL;
+  fill_geom(Ls[0], dir[0], 0, dims0, dims1, FLUPS_F64, true, FLUPS_CELL, 1);
+  Ls[0].p.in = rhs;
+  Ls[0].p.out = W1;
+  Ls[1].kind = K_FWD_C2C;
+  fill_geom(Ls[1], dir[1], 1, dims1, dims2, FLUPS_F64, false, FLUPS_CELL, 1);
+  Ls[1].p.in = W1;
+  Ls[1].p.out = W2;
+  Ls[2].kind = K_FUSED_C2C;
+  fill_geom(Ls[2], dir[2], 2, dims2, dims2, FLUPS_F64, false, FLUPS_CELL, 1);
+  Ls[2].p.in = W2;
+  Ls[2].p.out = W2;
+  {
+    FusedGreen& g = Ls[2].p.g;
+    g.stored = nullptr;
+    for (int d = 0; d < 3; ++d) {
+      g.tab[d] = tabs[d];
+      g.gext[d] = dir[d].gext;
+      g.fold[d] = dir[d].role == R_C2C ? dir[d].P : 0;
+    }
+    g.kernel = FLUPS_SPECTRAL;
+    g.scale = 1.0 / ((double)dir[0].P * dir[1].P * dir[2].P);
+    g.dims1 = dims2[1];
+    g.dims2 = dims2[2];
+  }
+  Ls[3].kind = K_INV_C2C;
+  fill_geom(Ls[3], dir[1], 1, dims2, dims1, FLUPS_F64, false, FLUPS_CELL, 1);
+  Ls[3].p.in = W2;
+  Ls[3].p.out = W1;
+  Ls[4].kind = K_INV_REAL;
+  fill_geom(Ls[4], dir[0], 0, dims1, dims0, FLUPS_F64, true, FLUPS_CELL, 1);
+  Ls[4].p.in = W1;
+  Ls[4].p.out = phi;
+  for (int i = 0; i < 5; ++i) {
+    if (Ls[i].smem > 227 * 1024 || Ls[i].nthr > 1024) return FLUPS_ESIZE;
+    cudaError_t e = launch_pass(Ls[i].kind, FLUPS_F64, Ls[i].p, Ls[i].grid, Ls[i].nthr, Ls[i].smem, st);
+    if (e) return cuda_fail(e, "noalloc pass launch");
+  }
+  return FLUPS_OK;
+}

@@ -26,7 +26,7 @@ KERNELS = {"spectral": SPECTRAL, "hej0": HEJ0, "hej2": HEJ2, "hej4": HEJ4, "hej6
 EXPORTED = (
     "flups_init_topo", "flups_topo_free", "flups_init_solver", "flups_setup", "flups_solve",
     "flups_solve_host", "flups_cleanup", "flups_solver_info", "flups_strerror", "flups_last_cuda_error",
-    "flups_debug_special", "flups_solve_pass", "flups_pass_info",
+    "flups_debug_special", "flups_solve_pass", "flups_pass_info", "flups_solve_periodic_noalloc",
 )
 
 
@@ -65,6 +65,7 @@ def lib():
         L.flups_debug_special.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int, ctypes.c_double]
         L.flups_solve_pass.argtypes = [vp, ctypes.c_int, vp, vp, vp]
         L.flups_pass_info.argtypes = [vp, ctypes.c_int, ip, ip, ip, dp, dp]
+        L.flups_solve_periodic_noalloc.argtypes = [vp, vp, ip, dp, vp]
         for name in EXPORTED:
             if name not in ("flups_strerror", "flups_last_cuda_error"):
                 getattr(L, name).restype = ctypes.c_int
@@ -171,6 +172,14 @@ def flups_pass_info(solver, i):
     _check(lib().flups_pass_info(solver, int(i), ctypes.byref(kind), ctypes.byref(axis), ctypes.byref(P),
                                  ctypes.byref(b), ctypes.byref(fl)), "flups_pass_info")
     return {"kind": kind.value, "axis": axis.value, "P": P.value, "bytes": b.value, "flops": fl.value}
+
+
+def flups_solve_periodic_noalloc(phi, rhs, n, L, stream=None):
+    """Allocation-free periodic FP64 solve (workspace in a fixed static device array)."""
+    nn = (ctypes.c_int * 3)(*[int(v) for v in n])
+    LL = (ctypes.c_double * 3)(*[float(v) for v in L])
+    _check(lib().flups_solve_periodic_noalloc(_ptr(phi), _ptr(rhs), nn, LL, _stream(stream)),
+           "flups_solve_periodic_noalloc")
 
 
 def flups_debug_special(which, x, y, out, n, eps):
