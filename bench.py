@@ -384,6 +384,25 @@ def run_ours(args):
     return 0
 
 
+def run_profile(args):
+    import torch
+
+    from paper_2211_07777_gb300 import flups as F
+    wl = workload(args.workload)
+    dt = torch.float32 if wl["prec"] == 0 else torch.float64
+    solver = F.Solver(wl["n"], wl["bc"], L=wl["L"], center=wl["center"], prec=wl["prec"], green=wl["kernel"],
+                      h=wl.get("h"))
+    rhs = torch.from_numpy(wl["rhs"]()).to("cuda", dt)
+    phi = torch.empty_like(rhs)
+    for _ in range(args.warmup + args.steps):
+        solver.solve(phi, rhs)
+    torch.cuda.synchronize()
+    solver.close()
+    print(json.dumps({"profile_run": args.workload, "solves": args.warmup + args.steps,
+                      "launches_per_solve": solver.info["launches"]}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -392,11 +411,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="unb128_f64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only W warm-up and K solves, no checks or side measurements (for ncu captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile(args)
     return run_ours(args)
 
 
