@@ -124,7 +124,10 @@ struct flups_solver_s {
   double h[3], L[3];
   int green, op, diff;
   double eps_over_h, eps;
-  int types[3];
+  int types[3];        // per direction, the (first component's) type that sets the plan's geometry
+  int tf[3][3];        // [comp][dir] transform type of the source
+  int tu[3][3];        // [comp][dir] transform type of the result (Biot-Savart: the curl's conditions)
+  void* dsym[3] = {nullptr, nullptr, nullptr};
   DirPlan dir[3];
   int order[3];
   int dims[3][3];     // array dims after 0, 1, 2 forward passes
@@ -205,10 +208,58 @@ ArrDesc arr_desc(const int* d, int axis) {
 
 int ilog2(int w) { int l = 0; while ((1 << l) < w) ++l; return l; }
 
+int pack3(int a, int b, int c) { return a | (b << 4) | (c << 8); }
+size_t esz(int prec) { return prec == FLUPS_F32 ? 4 : 8; }
+
+// Geometry family of a direction type: the components of a vector field must
+// share it per direction (same extension length and mode layout).
+int family(int t) {
+  switch (t) {
+    case T_PER: return 0;
+    case T_UNB: return 1;
+    case T_EE: case T_OO: return 2;
+    case T_EO: case T_OE: return 3;
+    case T_EU: case T_OU: return 4;
+    default: return 5;
+  }
+}
+
+int swap_parity(int b) { return b == FLUPS_EVEN ? FLUPS_ODD : (b == FLUPS_ODD ? FLUPS_EVEN : b); }
+
+// Derivative symbol per extension mode kk of a P-periodic direction: the
+// signed wavenumber w = 2 pi s/(P h), s = kk or kk - P, zero at the Nyquist
+// mode, or the finite-difference symbols (Section "Application: the
+// Biot-Savart solver"): order 2 sin(wh)/h, order 4 (4/3 sin wh - 1/6 sin 2wh)/h,
+// order 6 (3/2 sin wh - 3/10 sin 2wh + 1/30 sin 3wh)/h.
+int make_dsym(int P, double h, int diff, int prec, void** out) {
+  std::vector<double> v(P);
+  for (int kk = 0; kk < P; ++kk) {
+    const int sgn = (2 * kk <= P) ? kk : kk - P;
+    const double w = 2.0 * M_PI * sgn / (P * h);
+    double sym;
+    if (2 * kk == P) sym = 0.0;
+    else if (diff == FLUPS_DIFF_FD2) sym = std::sin(w * h) / h;
+    else if (diff == FLUPS_DIFF_FD4) sym = (4.0 / 3.0 * std::sin(w * h) - std::sin(2 * w * h) / 6.0) / h;
+    else if (diff == FLUPS_DIFF_FD6)
+      sym = (1.5 * std::sin(w * h) - 0.3 * std::sin(2 * w * h) + std::sin(3 * w * h) / 30.0) / h;
+    else sym = w;
+    v[kk] = sym;
+  }
+  const size_t bytes = (size_t)P * esz(prec);
+  CK(cudaMalloc(out, bytes));
+  if (prec == FLUPS_F32) {
+    std::vector<float> f(v.begin(), v.end());
+    CK(cudaMemcpy(*out, f.data(), bytes, cudaMemcpyHostToDevice));
+  } else {
+    CK(cudaMemcpy(*out, v.data(), bytes, cudaMemcpyHostToDevice));
+  }
+  return FLUPS_OK;
+}
+
 // Tile shape: W lanes (power of 2) per CTA within a 2 x 32 KB ping-pong
 // shared-memory budget; about one radix-16 butterfly per thread and stage.
-void tile_shape(int P, int prec, int npen, bool packed, int* W, int* nthr) {
-  const int budget = prec == FLUPS_F32 ? 4096 : 2048;  // complex elements per buffer
+void tile_shape(int P, int prec, int npen, bool packed, int* W, int* nthr, int share = 1) {
+  const int budget = (prec == FLUPS_F32 ? 4096 : 2048) / share;  // complex elements per buffer
   int w = 1;
   while (w * 2 * P <= budget && w < 64) w *= 2;
   int need = packed ? (npen + 1) / 2 : npen;
@@ -226,18 +277,19 @@ void tile_shape(int P, int prec, int npen, bool packed, int* W, int* nthr) {
 }
 
 void fill_geom(Launch& L, const DirPlan& dp, int axis, const int* din, const int* dout, int prec, bool packed,
-               int center, int ncomp) {
+               int center, int ncomp, int share = 1) {
   PassParams& p = L.p;
   p.ai = arr_desc(din, axis);
   p.ao = arr_desc(dout, axis);
   p.axis = axis;
   p.npen = axis == 0 ? din[1] * din[2] : din[0];
   int W, nthr;
-  tile_shape(dp.P, prec, p.npen, packed, &W, &nthr);
+  tile_shape(dp.P, prec, p.npen, packed, &W, &nthr, share);
   p.W = W;
   p.lw = ilog2(W);
   p.LS = (axis == 0 && W >= 8) ? W + 1 : W;
   p.type = dp.type;
+  p.ctypes = dp.type | (dp.type << 4) | (dp.type << 8);
   p.center = center;
   p.N = dp.N;
   p.n_data = dp.n_data;
@@ -430,6 +482,7 @@ int build_passes(flups_solver_s* s) {
     Launch L{};
     L.kind = K_FWD_REAL;
     fill_geom(L, s->dir[o[0]], o[0], s->dims[0], s->dims[1], prec, true, center, nc);
+    L.p.ctypes = pack3(s->tf[0][o[0]], s->tf[1][o[0]], s->tf[2][o[0]]);
     L.p.out = s->W1;
     L.user_in = 1;
     L.bytes = arr_bytes(0) + arr_bytes(1);
@@ -443,6 +496,7 @@ int build_passes(flups_solver_s* s) {
     const bool real = !s->cplx[1];
     L.kind = real ? K_FWD_REAL : K_FWD_C2C;
     fill_geom(L, s->dir[o[1]], o[1], s->dims[1], s->dims[2], prec, real, center, nc);
+    L.p.ctypes = pack3(s->tf[0][o[1]], s->tf[1][o[1]], s->tf[2][o[1]]);
     L.p.in = s->W1;
     L.p.out = s->W2;
     L.bytes = arr_bytes(1) + arr_bytes(2);
@@ -454,12 +508,28 @@ int build_passes(flups_solver_s* s) {
   {
     Launch L{};
     const bool real = !s->cplx[2];
-    L.kind = real ? K_FUSED_REAL : K_FUSED_C2C;
+    const bool curl = s->op == FLUPS_BIOT_SAVART;
+    L.kind = curl ? (real ? K_CURL_REAL : K_CURL_C2C) : (real ? K_FUSED_REAL : K_FUSED_C2C);
     const DirPlan& dp = s->dir[o[2]];
-    fill_geom(L, dp, o[2], s->dims[2], s->dims[2], prec, real, center, nc);
+    fill_geom(L, dp, o[2], s->dims[2], s->dims[2], prec, real, center, curl ? 1 : nc, curl ? 3 : 1);
+    L.p.ctypes = pack3(s->tf[0][o[2]], s->tf[1][o[2]], s->tf[2][o[2]]);
     L.p.in = s->W2;
     L.p.out = s->W2;
     FusedGreen& g = L.p.g;
+    if (curl) {
+      L.smem = 6 * (size_t)dp.P * L.p.LS * 2 * esize(prec) + (size_t)(real ? 2 : 1) * L.p.W * (prec == FLUPS_F32 ? 96 : 176) + 16;
+      g.utypes = pack3(s->tu[0][o[2]], s->tu[1][o[2]], s->tu[2][o[2]]);
+      for (int d = 0; d < 3; ++d) {
+        g.dsym[d] = s->dsym[d];
+        g.role[d] = s->dir[d].role;
+        g.quarter[d] = is_quarter_t(s->dir[d].type);
+        g.srcodd[d] = 0;
+        for (int c = 0; c < 3; ++c) {
+          const int t = s->tf[c][d];
+          if (t == T_OO || t == T_OE || t == T_OU || t == T_UO) g.srcodd[d] |= 1 << c;
+        }
+      }
+    }
     g.stored = s->green_dev;
     for (int d = 0; d < 3; ++d) {
       g.tab[d] = s->tabs[d];
@@ -483,6 +553,7 @@ int build_passes(flups_solver_s* s) {
     const bool real = !s->cplx[1];
     L.kind = real ? K_INV_REAL : K_INV_C2C;
     fill_geom(L, s->dir[o[1]], o[1], s->dims[2], s->dims[1], prec, real, center, nc);
+    L.p.ctypes = pack3(s->tu[0][o[1]], s->tu[1][o[1]], s->tu[2][o[1]]);
     L.p.in = s->W2;
     L.p.out = s->W1;
     L.bytes = arr_bytes(1) + arr_bytes(2);
@@ -495,6 +566,7 @@ int build_passes(flups_solver_s* s) {
     Launch L{};
     L.kind = K_INV_REAL;
     fill_geom(L, s->dir[o[0]], o[0], s->dims[1], s->dims[0], prec, true, center, nc);
+    L.p.ctypes = pack3(s->tu[0][o[0]], s->tu[1][o[0]], s->tu[2][o[0]]);
     L.p.in = s->W1;
     L.user_out = 1;
     L.bytes = arr_bytes(0) + arr_bytes(1);
@@ -557,7 +629,10 @@ int flups_init_solver(flups_topo t, const int* bc, const double h[3], const doub
                       double eps_over_h, int op, int diff, flups_solver* out) {
   if (!t || !bc || !h || !L || !out) return FLUPS_EINVAL;
   if (op != FLUPS_POISSON && op != FLUPS_BIOT_SAVART) return FLUPS_EINVAL;
-  if (op == FLUPS_BIOT_SAVART) return FLUPS_EINVAL;  // the curl path is added with its fused kernel
+  if (op == FLUPS_BIOT_SAVART && t->ncomp != 3) return FLUPS_EINVAL;
+  if (op == FLUPS_BIOT_SAVART && !(diff == FLUPS_DIFF_SPECTRAL || diff == FLUPS_DIFF_FD2 || diff == FLUPS_DIFF_FD4 ||
+                                   diff == FLUPS_DIFF_FD6))
+    return FLUPS_EINVAL;
   const int gk[] = {FLUPS_SPECTRAL, FLUPS_HEJ0, FLUPS_HEJ2, FLUPS_HEJ4, FLUPS_HEJ6, FLUPS_HEJ8, FLUPS_HEJ10, FLUPS_LGF2};
   bool gok = false;
   for (int g : gk) gok |= (g == green);
@@ -581,11 +656,39 @@ int flups_init_solver(flups_topo t, const int* bc, const double h[3], const doub
   s->eps_over_h = eps_over_h;
   s->eps = eps_over_h * std::fmax(h[0], std::fmax(h[1], h[2]));
   int rc = FLUPS_OK;
-  for (int d = 0; d < 3 && rc == FLUPS_OK; ++d) rc = classify(s->bc[0][d][0], s->bc[0][d][1], &s->types[d]);
-  // a vector Poisson solve shares one plan: every component needs the same conditions
-  for (int c = 1; c < t->ncomp && rc == FLUPS_OK; ++c)
-    for (int d = 0; d < 3; ++d)
-      if (s->bc[c][d][0] != s->bc[0][d][0] || s->bc[c][d][1] != s->bc[0][d][1]) rc = FLUPS_EBC;
+  for (int c = 0; c < t->ncomp && rc == FLUPS_OK; ++c)
+    for (int d = 0; d < 3 && rc == FLUPS_OK; ++d) rc = classify(s->bc[c][d][0], s->bc[c][d][1], &s->tf[c][d]);
+  for (int c = t->ncomp; c < 3; ++c)
+    for (int d = 0; d < 3; ++d) s->tf[c][d] = s->tf[0][d];
+  for (int d = 0; d < 3; ++d) s->types[d] = s->tf[0][d];
+  if (rc == FLUPS_OK && op == FLUPS_POISSON) {
+    // a vector Poisson solve shares one plan: every component needs the same conditions
+    for (int c = 1; c < t->ncomp && rc == FLUPS_OK; ++c)
+      for (int d = 0; d < 3; ++d)
+        if (s->bc[c][d][0] != s->bc[0][d][0] || s->bc[c][d][1] != s->bc[0][d][1]) rc = FLUPS_EBC;
+    for (int c = 0; c < 3; ++c)
+      for (int d = 0; d < 3; ++d) s->tu[c][d] = s->tf[c][d];
+  }
+  if (rc == FLUPS_OK && op == FLUPS_BIOT_SAVART) {
+    // one geometry per direction for the three components
+    for (int d = 0; d < 3 && rc == FLUPS_OK; ++d)
+      for (int c = 1; c < 3; ++c)
+        if (family(s->tf[c][d]) != family(s->tf[0][d])) rc = FLUPS_EBC;
+    // u_c = d_a f_b - d_b f_a: along d each term keeps its source's faces, with
+    // even/odd swapped along the differentiated direction; both terms must agree
+    for (int c = 0; c < 3 && rc == FLUPS_OK; ++c) {
+      const int a = (c + 1) % 3, b = (c + 2) % 3;
+      for (int d = 0; d < 3 && rc == FLUPS_OK; ++d) {
+        int f1[2], f2[2];
+        for (int f = 0; f < 2; ++f) {
+          f1[f] = d == a ? swap_parity(s->bc[b][d][f]) : s->bc[b][d][f];
+          f2[f] = d == b ? swap_parity(s->bc[a][d][f]) : s->bc[a][d][f];
+        }
+        if (f1[0] != f2[0] || f1[1] != f2[1]) rc = FLUPS_EBC;
+        else rc = classify(f1[0], f1[1], &s->tu[c][d]);
+      }
+    }
+  }
   if (rc == FLUPS_OK) rc = build_plan(s);
   if (rc == FLUPS_OK) {
     int du = 0;
@@ -607,11 +710,21 @@ int flups_setup(flups_solver s, void* stream, size_t* workspace_bytes) {
     if (workspace_bytes) *workspace_bytes = s->ws_bytes;
     return FLUPS_OK;
   }
-  std::call_once(g_limits_once, [] { g_limits_err = set_pass_smem_limits(); });
+  std::call_once(g_limits_once, [] {
+    g_limits_err = set_pass_smem_limits();
+    if (g_limits_err == cudaSuccess) g_limits_err = set_curl_smem_limits();
+  });
   if (g_limits_err) return cuda_fail(g_limits_err, "smem limits");
   cudaStream_t st = (cudaStream_t)stream;
   const int prec = s->topo.prec, nc = s->topo.ncomp;
   const size_t es = esize(prec);
+  if (s->op == FLUPS_BIOT_SAVART) {
+    for (int d = 0; d < 3; ++d) {
+      int rc = make_dsym(s->dir[d].P, s->dir[d].h, s->diff, prec, &s->dsym[d]);
+      if (rc) return rc;
+      s->ws_bytes += (size_t)s->dir[d].P * es;
+    }
+  }
   for (int d = 0; d < 3; ++d) {
     int rc = make_twiddles(s->dir[d].P, prec, &s->dir[d].tw);
     if (rc) return rc;
@@ -648,7 +761,8 @@ int flups_solve(flups_solver s, void* phi, const void* rhs, void* stream) {
     PassParams p = L.p;
     if (L.user_in) p.in = rhs;
     if (L.user_out) p.out = phi;
-    cudaError_t e = launch_pass(L.kind, prec, p, L.grid, L.nthr, L.smem, st);
+    cudaError_t e = L.kind >= K_CURL_REAL ? launch_curl(L.kind, prec, p, L.grid, L.nthr, L.smem, st)
+                                          : launch_pass(L.kind, prec, p, L.grid, L.nthr, L.smem, st);
     if (e) return cuda_fail(e, "pass launch");
   }
   return FLUPS_OK;
@@ -662,7 +776,9 @@ int flups_solve_pass(flups_solver s, int i, void* phi, const void* rhs, void* st
   PassParams p = L.p;
   if (L.user_in) p.in = rhs;
   if (L.user_out) p.out = phi;
-  cudaError_t e = launch_pass(L.kind, s->topo.prec, p, L.grid, L.nthr, L.smem, (cudaStream_t)stream);
+  cudaError_t e = L.kind >= K_CURL_REAL
+                      ? launch_curl(L.kind, s->topo.prec, p, L.grid, L.nthr, L.smem, (cudaStream_t)stream)
+                      : launch_pass(L.kind, s->topo.prec, p, L.grid, L.nthr, L.smem, (cudaStream_t)stream);
   if (e) return cuda_fail(e, "pass launch");
   return FLUPS_OK;
 }
@@ -706,6 +822,7 @@ int flups_cleanup(flups_solver s) {
   for (int d = 0; d < 3; ++d) {
     if (s->dir[d].tw) cudaFree(s->dir[d].tw);
     if (s->tabs[d]) cudaFree(s->tabs[d]);
+    if (s->dsym[d]) cudaFree(s->dsym[d]);
   }
   if (s->W1) cudaFree(s->W1);
   if (s->W2) cudaFree(s->W2);

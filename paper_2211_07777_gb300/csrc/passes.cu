@@ -15,172 +15,10 @@
 // half-sample phase exp(-i pi k/P) for cell-centred data.
 #include <cuda_runtime.h>
 
+#include "pass_common.cuh"
 #include "passes.cuh"
 
 namespace flups {
-
-// Largest block the planner launches: 512 threads (FP32) and 256 (FP64).
-template <typename T> struct MaxThreads { static constexpr int value = 512; };
-template <> struct MaxThreads<double> { static constexpr int value = 256; };
-
-// ---------------------------------------------------------------------------
-// Extension geometry (Sections 2.2, 2.3).  Data index i (already mirrored for
-// the unbounded-left semi types) -> positions and signs in the extension.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int base_type(int t) {
-  return t == T_UE ? T_EU : (t == T_UO ? T_OU : t);
-}
-
-__device__ __forceinline__ int images(int t, int center, int N, int i, int* pos, int* sg) {
-  int n = 0;
-  if (center == C_CELL) {
-    switch (t) {
-      case T_PER: case T_UNB: pos[0] = i; sg[0] = 1; return 1;
-      case T_EE: pos[0] = i; sg[0] = 1; pos[1] = 2 * N - 1 - i; sg[1] = 1; return 2;
-      case T_OO: pos[0] = i; sg[0] = 1; pos[1] = 2 * N - 1 - i; sg[1] = -1; return 2;
-      case T_EO:
-        pos[0] = i; sg[0] = 1; pos[1] = 2 * N - 1 - i; sg[1] = -1;
-        pos[2] = 2 * N + i; sg[2] = -1; pos[3] = 4 * N - 1 - i; sg[3] = 1; return 4;
-      case T_OE:
-        pos[0] = i; sg[0] = 1; pos[1] = 2 * N - 1 - i; sg[1] = 1;
-        pos[2] = 2 * N + i; sg[2] = -1; pos[3] = 4 * N - 1 - i; sg[3] = -1; return 4;
-      case T_EU: pos[0] = i; sg[0] = 1; pos[1] = 4 * N - 1 - i; sg[1] = 1; return 2;
-      case T_OU: pos[0] = i; sg[0] = 1; pos[1] = 4 * N - 1 - i; sg[1] = -1; return 2;
-    }
-    return 0;
-  }
-  switch (t) {
-    case T_PER: if (i < N) { pos[0] = i; sg[0] = 1; return 1; } return 0;
-    case T_UNB: pos[0] = i; sg[0] = 1; return 1;
-    case T_EE:
-      pos[n] = i; sg[n++] = 1;
-      if (i > 0 && i < N) { pos[n] = 2 * N - i; sg[n++] = 1; }
-      return n;
-    case T_OO:
-      if (i > 0 && i < N) { pos[0] = i; sg[0] = 1; pos[1] = 2 * N - i; sg[1] = -1; return 2; }
-      return 0;
-    case T_OE:
-      if (i >= 1) { pos[n] = i; sg[n++] = 1; pos[n] = 2 * N + i; sg[n++] = -1; }
-      if (i >= 1 && i <= N - 1) { pos[n] = 2 * N - i; sg[n++] = 1; pos[n] = 4 * N - i; sg[n++] = -1; }
-      return n;
-    case T_EO:
-      if (i <= N - 1) { pos[n] = i; sg[n++] = 1; pos[n] = 2 * N - i; sg[n++] = -1; }
-      if (i >= 1 && i <= N - 1) { pos[n] = 2 * N + i; sg[n++] = -1; pos[n] = 4 * N - i; sg[n++] = 1; }
-      return n;
-    case T_EU:
-      pos[n] = i; sg[n++] = 1;
-      if (i >= 1) { pos[n] = 4 * N - i; sg[n++] = 1; }
-      return n;
-    case T_OU:
-      if (i >= 1) { pos[0] = i; sg[0] = 1; pos[1] = 4 * N - i; sg[1] = -1; return 2; }
-      return 0;
-  }
-  return 0;
-}
-
-// Positions of the extension that hold zeros (padding, odd faces); up to 3 ranges.
-__device__ __forceinline__ int zero_ranges(int t, int center, int N, int* lo, int* hi) {
-  if (center == C_CELL) {
-    if (t == T_UNB) { lo[0] = N; hi[0] = 2 * N; return 1; }
-    if (t == T_EU || t == T_OU) { lo[0] = N; hi[0] = 3 * N; return 1; }
-    return 0;
-  }
-  switch (t) {
-    case T_UNB: lo[0] = N + 1; hi[0] = 2 * N; return 1;
-    case T_OO: lo[0] = 0; hi[0] = 1; lo[1] = N; hi[1] = N + 1; return 2;
-    case T_OE: lo[0] = 0; hi[0] = 1; lo[1] = 2 * N; hi[1] = 2 * N + 1; return 2;
-    case T_EO: lo[0] = N; hi[0] = N + 1; lo[1] = 3 * N; hi[1] = 3 * N + 1; return 2;
-    case T_EU: lo[0] = N + 1; hi[0] = 3 * N; return 1;
-    case T_OU: lo[0] = 0; hi[0] = 1; lo[1] = N + 1; hi[1] = 3 * N; return 2;
-  }
-  return 0;
-}
-
-// Extension position holding data index i on output, or -1 when the value is
-// forced to 0 (odd node face).  Node periodic phi_N := phi_0 (Section 2.1).
-__device__ __forceinline__ int primary_pos(int t, int center, int N, int i) {
-  if (center == C_NODE) {
-    if (t == T_PER && i == N) return 0;
-    if ((t == T_OO) && (i == 0 || i == N)) return -1;
-    if ((t == T_OE || t == T_OU) && i == 0) return -1;
-    if (t == T_EO && i == N) return -1;
-  }
-  return i;
-}
-
-// ---------------------------------------------------------------------------
-// Shared helpers.
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void zero_fill(cpx<T>* S, int LS, int W, int lo, int hi, int tid, int nthr) {
-  const int tot = (hi - lo) * W;
-  for (int idx = tid; idx < tot; idx += nthr) {
-    const int lane = idx % W;
-    const int j = lo + idx / W;
-    S[j * LS + lane] = mk<T>((T)0, (T)0);
-  }
-}
-
-// Build the two-pencil extension of real data (pencils q0 + c, c < 2W).
-template <typename T>
-__device__ __forceinline__ void load_real_ext(const PassParams& p, const T* __restrict__ in, cpx<T>* S, int q0,
-                                              int tid, int nthr) {
-  const int W = p.W, LS = p.LS, N = p.N, nd = p.n_data;
-  const int t = base_type(p.type);
-  const bool rev = is_reversed(p.type);
-  int lo[3], hi[3];
-  const int nz = zero_ranges(t, p.center, N, lo, hi);
-  for (int r = 0; r < nz; ++r) zero_fill<T>(S, LS, W, lo[r], hi[r], tid, nthr);
-  T* Sr = reinterpret_cast<T*>(S);
-  const int W2 = 2 * W;
-  const int tot = nd * W2;
-  const bool rowmode = p.axis == 0;
-  for (int idx = tid; idx < tot; idx += nthr) {
-    int c, i;
-    if (rowmode) { i = idx % nd; c = idx / nd; } else { c = idx % W2; i = idx / W2; }
-    const int q = q0 + c;
-    T v = (T)0;
-    if (q < p.npen) v = in[(long long)q * p.ai.ls + (long long)i * p.ai.js];
-    const int ii = rev ? nd - 1 - i : i;
-    int pos[4], sg[4];
-    const int n = images(t, p.center, N, ii, pos, sg);
-    const int lane = c >> 1, part = c & 1;
-    for (int k = 0; k < n; ++k) Sr[2 * (pos[k] * LS + lane) + part] = sg[k] > 0 ? v : -v;
-  }
-}
-
-// Store data values of both pencils of every lane from the inverse-transformed extension.
-template <typename T>
-__device__ __forceinline__ void store_real_data(const PassParams& p, T* __restrict__ out, const cpx<T>* S, int q0,
-                                                int tid, int nthr) {
-  const int W = p.W, N = p.N, nd = p.n_data;
-  const int t = base_type(p.type);
-  const bool rev = is_reversed(p.type);
-  const int W2 = 2 * W;
-  const int tot = nd * W2;
-  const bool rowmode = p.axis == 0;
-  for (int idx = tid; idx < tot; idx += nthr) {
-    int c, i;
-    if (rowmode) { i = idx % nd; c = idx / nd; } else { c = idx % W2; i = idx / W2; }
-    const int q = q0 + c;
-    if (q >= p.npen) continue;
-    const int ii = rev ? nd - 1 - i : i;
-    const int pos = primary_pos(t, p.center, N, ii);
-    T v = (T)0;
-    if (pos >= 0) {
-      const cpx<T> z = S[pos * p.LS + (c >> 1)];
-      v = (c & 1) ? z.y : z.x;
-    }
-    out[(long long)q * p.ao.ls + (long long)i * p.ao.js] = v;
-  }
-}
-
-// Spectrum of pencil a (part 0) or b (part 1) at mode k from the packed FFT.
-template <typename T>
-__device__ __forceinline__ cpx<T> split(cpx<T> zk, cpx<T> zm, int part) {
-  const T h = (T)0.5;
-  return part == 0 ? mk<T>(h * (zk.x + zm.x), h * (zk.y - zm.y)) : mk<T>(h * (zk.y + zm.y), h * (zm.x - zk.x));
-}
 
 // ---------------------------------------------------------------------------
 // Forward pass on real data: R2C (periodic, doubled unbounded) or r2r
@@ -195,12 +33,13 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, 1) k_fwd_real(PassParams
   const int q0 = blockIdx.x * 2 * W;
   const long long obase_i = (long long)blockIdx.y * p.ai.os + (long long)blockIdx.z * p.ai.cs;
   const long long obase_o = (long long)blockIdx.y * p.ao.os + (long long)blockIdx.z * p.ao.cs;
-  load_real_ext<T>(p, (const T*)p.in + obase_i, S, q0, tid, nthr);
+  const int ctype = comp_type(p, blockIdx.z);
+  load_real_ext<T>(p, ctype, (const T*)p.in + obase_i, S, q0, tid, nthr);
   __syncthreads();
   const cpx<T>* tw = (const cpx<T>*)p.tw;
   S = fft_tile<T, false>(S, S + (size_t)P * LS, LS, P, W, p.lw, p.plan, tw, tid, nthr);
 
-  const int t = base_type(p.type);
+  const int t = base_type(ctype);
   const bool cplx_out = (t == T_PER || t == T_UNB);
   const bool quarter = is_quarter(t);
   const bool oddo = is_odd_origin(t);
@@ -232,9 +71,9 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, 1) k_fwd_real(PassParams
 
 // Spectrum value X_kk of one pencil rebuilt from its stored modes (inverse of the above).
 template <typename T>
-__device__ __forceinline__ cpx<T> stored_mode(const PassParams& p, const void* in, long long off_pencil, int kk,
-                                              const cpx<T>* tw) {
-  const int t = base_type(p.type);
+__device__ __forceinline__ cpx<T> stored_mode(const PassParams& p, int type, const void* in, long long off_pencil,
+                                              int kk, const cpx<T>* tw) {
+  const int t = base_type(type);
   if (t == T_PER || t == T_UNB) {
     cpx<T> X = ((const cpx<T>*)in)[off_pencil + (long long)kk * p.ai.js];
     if (kk == 0 || 2 * kk == p.P) X.y = (T)0;  // DC and Nyquist of a real signal are real
@@ -263,6 +102,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, 1) k_inv_real(PassParams
   const long long obase_i = (long long)blockIdx.y * p.ai.os + (long long)blockIdx.z * p.ai.cs;
   const long long obase_o = (long long)blockIdx.y * p.ao.os + (long long)blockIdx.z * p.ao.cs;
   const cpx<T>* tw = (const cpx<T>*)p.tw;
+  const int ctype = comp_type(p, blockIdx.z);
   const int half = P / 2;
   const int tot = (half + 1) * W;
   const bool rowmode = p.axis == 0;
@@ -271,52 +111,19 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, 1) k_inv_real(PassParams
     if (rowmode) { k = idx % (half + 1); lane = idx / (half + 1); } else { lane = idx % W; k = idx / W; }
     const int qa = q0 + 2 * lane, qb = qa + 1;
     cpx<T> Xa = mk<T>((T)0, (T)0), Xb = Xa;
-    if (qa < p.npen) Xa = stored_mode<T>(p, p.in, obase_i + (long long)qa * p.ai.ls, k, tw);
-    if (qb < p.npen) Xb = stored_mode<T>(p, p.in, obase_i + (long long)qb * p.ai.ls, k, tw);
+    if (qa < p.npen) Xa = stored_mode<T>(p, ctype, p.in, obase_i + (long long)qa * p.ai.ls, k, tw);
+    if (qb < p.npen) Xb = stored_mode<T>(p, ctype, p.in, obase_i + (long long)qb * p.ai.ls, k, tw);
     S[k * LS + lane] = mk<T>(Xa.x - Xb.y, Xa.y + Xb.x);
     if (k != 0 && 2 * k != P) S[(P - k) * LS + lane] = mk<T>(Xa.x + Xb.y, Xb.x - Xa.y);
   }
   __syncthreads();
   S = fft_tile<T, true>(S, S + (size_t)P * LS, LS, P, W, p.lw, p.plan, tw, tid, nthr);
-  store_real_data<T>(p, (T*)p.out + obase_o, S, q0, tid, nthr);
+  store_real_data<T>(p, ctype, (T*)p.out + obase_o, S, q0, tid, nthr);
 }
 
 // ---------------------------------------------------------------------------
 // Complex passes (second and third complex directions).
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void load_cplx(const PassParams& p, const cpx<T>* __restrict__ in, cpx<T>* S, int q0,
-                                          int tid, int nthr) {
-  const int W = p.W, LS = p.LS, nu = p.n_use;
-  if (nu < p.P) zero_fill<T>(S, LS, W, nu, p.P, tid, nthr);
-  const int tot = nu * W;
-  const bool rowmode = p.axis == 0;
-  for (int idx = tid; idx < tot; idx += nthr) {
-    int lane, i;
-    if (rowmode) { i = idx % nu; lane = idx / nu; } else { lane = idx % W; i = idx / W; }
-    const int q = q0 + lane;
-    cpx<T> v = mk<T>((T)0, (T)0);
-    if (q < p.npen) v = in[(long long)q * p.ai.ls + (long long)i * p.ai.js];
-    S[i * LS + lane] = v;
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void store_cplx_data(const PassParams& p, cpx<T>* __restrict__ out, const cpx<T>* S, int q0,
-                                                int tid, int nthr) {
-  const int W = p.W, LS = p.LS, nd = p.n_data;
-  const int tot = nd * W;
-  const bool rowmode = p.axis == 0;
-  for (int idx = tid; idx < tot; idx += nthr) {
-    int lane, i;
-    if (rowmode) { i = idx % nd; lane = idx / nd; } else { lane = idx % W; i = idx / W; }
-    const int q = q0 + lane;
-    if (q >= p.npen) continue;
-    const int pos = (p.type == T_PER && p.center == C_NODE && i == p.N) ? 0 : i;
-    out[(long long)q * p.ao.ls + (long long)i * p.ao.js] = S[pos * LS + lane];
-  }
-}
-
 template <typename T>
 __global__ void __launch_bounds__(MaxThreads<T>::value, 1) k_fwd_c2c(PassParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -462,11 +269,12 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, 1) k_fused_real(PassPara
   const int q0 = blockIdx.x * 2 * W;
   const long long obase = (long long)blockIdx.y * p.ai.os + (long long)blockIdx.z * p.ai.cs;
   for (int c = tid; c < 2 * W; c += nthr) pencil_green_base<T>(p, q0 + c, blockIdx.y, &goff[c], &k2p[c]);
-  load_real_ext<T>(p, (const T*)p.in + obase, S, q0, tid, nthr);
+  const int ctype = comp_type(p, blockIdx.z);
+  load_real_ext<T>(p, ctype, (const T*)p.in + obase, S, q0, tid, nthr);
   __syncthreads();
   const cpx<T>* tw = (const cpx<T>*)p.tw;
   cpx<T>* X = fft_tile<T, false>(S, S2, LS, P, W, p.lw, p.plan, tw, tid, nthr);
-  const bool quarter = is_quarter(base_type(p.type));
+  const bool quarter = is_quarter(base_type(ctype));
   const int half = P / 2;
   const int tot = (half + 1) * W;
   for (int idx = tid; idx < tot; idx += nthr) {
@@ -489,7 +297,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, 1) k_fused_real(PassPara
   }
   __syncthreads();
   X = fft_tile<T, true>(X, X == S ? S2 : S, LS, P, W, p.lw, p.plan, tw, tid, nthr);
-  store_real_data<T>(p, (T*)p.out + obase, X, q0, tid, nthr);
+  store_real_data<T>(p, ctype, (T*)p.out + obase, X, q0, tid, nthr);
 }
 
 // ---------------------------------------------------------------------------

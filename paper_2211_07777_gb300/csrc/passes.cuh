@@ -41,6 +41,12 @@ struct FusedGreen {
   double scale;           // 1 / (P1 P2 P3) (closed form only; the stored spectrum is pre-scaled)
   int quarter3;           // the fused direction is a quarter-wave type
   int dims1, dims2;       // for axis-0 passes: y extent of the array (row -> (y, z))
+  // Biot-Savart (spectral curl) only
+  int utypes;             // transform type of each output component along the fused axis (4 bits each)
+  const void* dsym[3];    // derivative symbol of extension mode kk, per direction (signed, 0 at Nyquist)
+  int role[3];            // per direction: 0 r2r coefficients, 1 R2C modes, 2 C2C modes
+  int quarter[3];         // per direction: quarter-wave r2r (stored m <-> extension mode 2m + 1)
+  int srcodd[3];          // per direction: bit c set when component c's source type is odd at the origin
 };
 
 struct PassParams {
@@ -51,6 +57,7 @@ struct PassParams {
   int npen;               // pencils along the lane dimension
   int W, lw, LS;          // lanes per tile (power of 2), log2, smem lane stride
   int type, center, N, n_data, P, n_modes;
+  int ctypes;             // transform type of each vector component, 4 bits per component
   int n_use;              // data values used (node periodic: N)
   RadixPlan plan;
   const void* tw;         // exp(-2 pi i m/(2P)), m < 2P, path precision
@@ -58,7 +65,12 @@ struct PassParams {
 };
 
 // host launchers (passes.cu)
-enum PassKind : int { K_FWD_REAL = 0, K_INV_REAL = 1, K_FWD_C2C = 2, K_INV_C2C = 3, K_FUSED_REAL = 4, K_FUSED_C2C = 5 };
+enum PassKind : int {
+  K_FWD_REAL = 0, K_INV_REAL = 1, K_FWD_C2C = 2, K_INV_C2C = 3, K_FUSED_REAL = 4, K_FUSED_C2C = 5,
+  K_CURL_REAL = 6, K_CURL_C2C = 7
+};
+cudaError_t launch_curl(int kind, int prec, const PassParams& p, dim3 grid, int nthreads, size_t smem, cudaStream_t st);
+cudaError_t set_curl_smem_limits();
 cudaError_t launch_pass(int kind, int prec, const PassParams& p, dim3 grid, int nthreads, size_t smem, cudaStream_t st);
 cudaError_t set_pass_smem_limits();
 

@@ -56,6 +56,22 @@ def periodic_sines(n, modes, L=1.0, center=CELL, dtype=np.float64):
     return f
 
 
+def periodic_sines_torch(n, modes, device, dtype, L=1.0, center=CELL):
+    """The same field built on a device with torch (for the 1024^3 workload)."""
+    import torch
+    nx, ny, nz = n
+    x = torch.as_tensor(coords(nx, L, center), device=device, dtype=torch.float64)
+    y = torch.as_tensor(coords(ny, L, center), device=device, dtype=torch.float64)
+    z = torch.as_tensor(coords(nz, L, center), device=device, dtype=torch.float64)
+    f = torch.zeros((nz, ny, nx), device=device, dtype=dtype)
+    for a, b, c, A in modes:
+        sx = torch.sin(2 * math.pi * a * x / L).to(dtype)
+        sy = torch.sin(2 * math.pi * b * y / L).to(dtype)
+        sz = torch.sin(2 * math.pi * c * z / L).to(dtype)
+        f += A * sz[:, None, None] * sy[None, :, None] * sx[None, None, :]
+    return f
+
+
 def periodic_sines_planes(n, modes, zidx, L=1.0, center=CELL):
     """The same field restricted to the z-planes zidx (for sampled checks at large n)."""
     nx, ny, nz = n
