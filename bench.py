@@ -384,6 +384,63 @@ def run_ours(args):
     return 0
 
 
+def run_served(args):
+    """Served stream: 4096 seeded requests, sizes {32..256}^3, random face conditions, 30% Biot-Savart,
+    FP32/FP64 50/50; closed-loop capacity, then Poisson arrivals at 0.8x capacity."""
+    import torch
+
+    from paper_2211_07777_gb300 import flups as F
+    from paper_2211_07777_gb300 import serve
+    nreq = args.served_requests
+    reqs = W.served_stream(nreq=nreq, seed=4)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(min(free * 0.6, 96 << 30))
+    pool = serve.HostPool()
+    for r in reqs:
+        pool.input(r)
+    warm = serve.run_stream(reqs[:64], budget, nstreams=args.streams, closed_loop=True, pool=pool)
+    cap = serve.run_stream(reqs, budget, nstreams=args.streams, closed_loop=True, pool=pool)
+    rate = 0.8 * cap["req_per_s"]
+    nominal = 1.0 / np.mean(np.diff([r.arrival_s for r in reqs]))
+    with ClockSampler(0) as clk:
+        run = serve.run_stream(reqs, budget, nstreams=args.streams, time_scale=nominal / rate, pool=pool)
+    # FP32 against FP64 on sampled request classes (same input), the stated error of the FP32 path
+    errs = []
+    for r in [q for q in reqs if q.prec == F.F32][:8]:
+        outs = []
+        for prec in (F.F32, F.F64):
+            rr = W.Request(**{**r.__dict__, "prec": prec})
+            creq = serve.c_request(rr)
+            bc = [[tuple(creq.bc[(c * 3 + d) * 2:(c * 3 + d) * 2 + 2]) for d in range(3)] for c in range(3)]
+            sol = F.Solver(rr.n, bc if rr.op == 1 else bc[0], prec=prec, op=rr.op, green=rr.kernel)
+            dt = torch.float32 if prec == F.F32 else torch.float64
+            rhs = torch.from_numpy(np.ascontiguousarray(W.request_rhs(rr))).to("cuda", dt)
+            phi = torch.empty_like(rhs)
+            sol.solve(phi, rhs)
+            torch.cuda.synchronize()
+            outs.append(phi.double().cpu().numpy())
+            sol.close()
+        errs.append(float(np.abs(outs[0] - outs[1]).max() / np.abs(outs[1]).max()))
+    for k in ("outputs",):
+        run.pop(k, None)
+    line = {
+        "metric": "served throughput (Mpts/s) with p50/p99 latency", "value": run["mpts_per_s"], "unit": "Mpts/s",
+        "n_gpus": 1, "steps": nreq, "warmup": 64, "ms_per_step": run["makespan_s"] * 1e3 / nreq,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"served stream: {nreq} seeded requests, sizes uniform on {{32..256}}^3, random face "
+                               "conditions, 30% Biot-Savart Gaussian rings, FP32/FP64 50/50, Poisson arrivals at "
+                               "0.8x measured capacity", "name": "served", "hbm_budget_bytes": budget,
+                   "streams": args.streams},
+        "p50_ms": run["p50_ms"], "p99_ms": run["p99_ms"], "req_per_s": run["req_per_s"],
+        "fp32": run.get("fp32"), "fp64": run.get("fp64"),
+        "capacity_req_per_s": cap["req_per_s"], "capacity_mpts_per_s": cap["mpts_per_s"],
+        "fp32_vs_fp64_max_rel_err": max(errs) if errs else None,
+        "server": run["server"], "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_profile(args):
     import torch
 
@@ -411,6 +468,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="unb128_f64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--served-requests", type=int, default=4096)
+    ap.add_argument("--streams", type=int, default=8)
     ap.add_argument("--profile", action="store_true",
                     help="only W warm-up and K solves, no checks or side measurements (for ncu captures)")
     args = ap.parse_args()
@@ -420,6 +479,8 @@ def main():
         return run_reference(args)
     if args.profile:
         return run_profile(args)
+    if args.workload == "served":
+        return run_served(args)
     return run_ours(args)
 
 

@@ -156,6 +156,63 @@ int flups_pass_info(flups_solver s, int i, int* kind, int* axis, int* fft_len, d
  * `stream`; returns without synchronising. */
 int flups_solve_periodic_noalloc(double* phi, const double* rhs, const int n[3], const double L[3], void* stream);
 
+/* Plans shared by several concurrent solves (the serving runtime uses these).
+ * flups_setup_shared: like flups_setup but allocates no workspace; solves then
+ * go through flups_solve_ws with a caller-owned device workspace of
+ * flups_workspace_size bytes (256-byte aligned), so one plan (twiddles, Green
+ * spectrum) serves any number of solves in flight on different streams, each
+ * with its own workspace.  flups_solver_memory (host-only, after
+ * flups_init_solver): device bytes the plan keeps resident, the transient
+ * peak of its setup, and the workspace of one solve. */
+int flups_setup_shared(flups_solver s, void* stream);
+int flups_workspace_size(flups_solver s, size_t* bytes);
+int flups_solve_ws(flups_solver s, void* phi, const void* rhs, void* workspace, void* stream);
+int flups_solver_memory(flups_solver s, size_t* resident, size_t* transient, size_t* workspace);
+
+/* ---- Serving: continuous batching of independent solves -------------------
+ * A request describes one solve (same fields as flups_init_topo/init_solver;
+ * scalar problems use bc[0]).  Its host arrays are read (rhs) and written
+ * (phi) asynchronously: they must stay valid, and pinned for full copy
+ * bandwidth, until the request's ticket is reported done.  Requests are
+ * admitted as slots and memory free up within the device-memory budget given
+ * at creation; admitted requests run concurrently on `nstreams` streams.
+ * Plans (Green spectra, twiddles) are cached per problem and evicted least
+ * recently used when memory is needed.  Not thread safe: one host thread
+ * drives a server. */
+typedef struct {
+  int n[3];
+  int center, prec, op, diff;
+  int bc[3][3][2];
+  double h[3], L[3];
+  int green;
+  double eps_over_h;
+} flups_request;
+
+typedef struct {
+  long long submitted, admitted, completed, rejected, failed, queued_max;
+  long long plan_hits, plan_misses, slots_created, evictions, plans_cached;
+  size_t hbm_in_use, hbm_peak;
+} flups_server_stats;
+
+typedef struct flups_server_s* flups_server;
+
+int flups_server_create(size_t hbm_budget_bytes, int nstreams, flups_server* out);
+/* Queues the request and admits what fits.  Returns FLUPS_EBC/ESIZE/EGREEN/
+ * EINVAL for an invalid request and FLUPS_ENOMEM if it cannot fit the budget
+ * even alone (nothing is queued then). */
+int flups_server_submit(flups_server sv, const flups_request* rq, const void* rhs_host, void* phi_host,
+                        long long* ticket);
+/* Completed tickets since the last call (up to max): latency from submission
+ * to the end of the result's copy to the host, in seconds, and the status
+ * (FLUPS_OK, or an error with latency -1).  poll never blocks; wait blocks
+ * until at least one ticket completes or nothing is left. */
+int flups_server_poll(flups_server sv, long long* tickets, double* latency_s, int* status, int max, int* n_done);
+int flups_server_wait(flups_server sv, long long* tickets, double* latency_s, int* status, int max, int* n_done);
+int flups_server_pending(flups_server sv, int* queued, int* running);
+int flups_server_get_stats(flups_server sv, flups_server_stats* out);
+/* Waits for the requests in flight, then frees every plan, slot and stream. */
+int flups_server_destroy(flups_server sv);
+
 /* Text of a status code (static storage). */
 const char* flups_strerror(int status);
 /* Text of the last CUDA error seen by the library in this process (static storage). */

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -108,6 +109,7 @@ struct Launch {
   int nthr;
   size_t smem;
   int user_in, user_out;  // 1: the pointer is the caller's rhs / phi
+  int in_buf, out_buf;    // workspace buffer read / written: 1 = W1, 2 = W2, 0 = none
   double bytes, flops;    // algorithmic bytes moved and nominal FFT flops (5 P log2 P per complex FFT)
 };
 
@@ -143,6 +145,8 @@ struct flups_solver_s {
   size_t ws_bytes = 0;
   std::vector<Launch> passes;
   bool ready = false;
+  bool shared = false;    // set up without its own workspace (solves pass one in)
+  size_t ws_need = 0;     // bytes of workspace one solve needs (W1 + W2, 256-aligned)
 };
 
 namespace {
@@ -484,6 +488,7 @@ int build_passes(flups_solver_s* s) {
     fill_geom(L, s->dir[o[0]], o[0], s->dims[0], s->dims[1], prec, true, center, nc);
     L.p.ctypes = pack3(s->tf[0][o[0]], s->tf[1][o[0]], s->tf[2][o[0]]);
     L.p.out = s->W1;
+    L.out_buf = 1;
     L.user_in = 1;
     L.bytes = arr_bytes(0) + arr_bytes(1);
     L.flops = ffts(L, true, 1);
@@ -499,6 +504,8 @@ int build_passes(flups_solver_s* s) {
     L.p.ctypes = pack3(s->tf[0][o[1]], s->tf[1][o[1]], s->tf[2][o[1]]);
     L.p.in = s->W1;
     L.p.out = s->W2;
+    L.in_buf = 1;
+    L.out_buf = 2;
     L.bytes = arr_bytes(1) + arr_bytes(2);
     L.flops = ffts(L, real, 1);
     s->passes.push_back(L);
@@ -515,6 +522,8 @@ int build_passes(flups_solver_s* s) {
     L.p.ctypes = pack3(s->tf[0][o[2]], s->tf[1][o[2]], s->tf[2][o[2]]);
     L.p.in = s->W2;
     L.p.out = s->W2;
+    L.in_buf = 2;
+    L.out_buf = 2;
     FusedGreen& g = L.p.g;
     if (curl) {
       L.smem = 6 * (size_t)dp.P * L.p.LS * 2 * esize(prec) + (size_t)(real ? 2 : 1) * L.p.W * (prec == FLUPS_F32 ? 96 : 176) + 16;
@@ -556,6 +565,8 @@ int build_passes(flups_solver_s* s) {
     L.p.ctypes = pack3(s->tu[0][o[1]], s->tu[1][o[1]], s->tu[2][o[1]]);
     L.p.in = s->W2;
     L.p.out = s->W1;
+    L.in_buf = 2;
+    L.out_buf = 1;
     L.bytes = arr_bytes(1) + arr_bytes(2);
     L.flops = ffts(L, real, 1);
     s->passes.push_back(L);
@@ -568,6 +579,7 @@ int build_passes(flups_solver_s* s) {
     fill_geom(L, s->dir[o[0]], o[0], s->dims[1], s->dims[0], prec, true, center, nc);
     L.p.ctypes = pack3(s->tu[0][o[0]], s->tu[1][o[0]], s->tu[2][o[0]]);
     L.p.in = s->W1;
+    L.in_buf = 1;
     L.user_out = 1;
     L.bytes = arr_bytes(0) + arr_bytes(1);
     L.flops = ffts(L, true, 1);
@@ -730,16 +742,22 @@ int flups_setup(flups_solver s, void* stream, size_t* workspace_bytes) {
     if (rc) return rc;
     s->ws_bytes += (size_t)4 * s->dir[d].P * es;
   }
-  for (int i = 1; i <= 2; ++i) {
-    const size_t n = (size_t)s->dims[i][0] * s->dims[i][1] * s->dims[i][2] * nc * (s->cplx[i] ? 2 : 1);
-    void** buf = i == 1 ? &s->W1 : &s->W2;
-    cudaError_t e = cudaMalloc(buf, n * es);
-    if (e == cudaErrorMemoryAllocation) {
-      cudaGetLastError();
-      return FLUPS_ENOMEM;
+  size_t wbytes[3] = {0, 0, 0};
+  for (int i = 1; i <= 2; ++i)
+    wbytes[i] = (((size_t)s->dims[i][0] * s->dims[i][1] * s->dims[i][2] * nc * (s->cplx[i] ? 2 : 1) * es) + 255) &
+                ~(size_t)255;
+  s->ws_need = wbytes[1] + wbytes[2];
+  if (!s->shared) {
+    for (int i = 1; i <= 2; ++i) {
+      void** buf = i == 1 ? &s->W1 : &s->W2;
+      cudaError_t e = cudaMalloc(buf, wbytes[i]);
+      if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return FLUPS_ENOMEM;
+      }
+      if (e) return cuda_fail(e, "workspace alloc");
+      s->ws_bytes += wbytes[i];
     }
-    if (e) return cuda_fail(e, "workspace alloc");
-    s->ws_bytes += n * es;
   }
   int rc = setup_green(s, st);
   if (rc) return rc;
@@ -752,13 +770,21 @@ int flups_setup(flups_solver s, void* stream, size_t* workspace_bytes) {
   return FLUPS_OK;
 }
 
-int flups_solve(flups_solver s, void* phi, const void* rhs, void* stream) {
-  if (!s || !phi || !rhs) return FLUPS_EINVAL;
-  if (!s->ready) return FLUPS_ESTATE;
+// Launch the whole pass list with the given workspace (W1 at ws, W2 after it).
+static int solve_impl(flups_solver s, void* phi, const void* rhs, void* ws, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const int prec = s->topo.prec;
+  void* W[3] = {nullptr, s->W1, s->W2};
+  if (ws) {
+    const size_t w1 = (((size_t)s->dims[1][0] * s->dims[1][1] * s->dims[1][2] * s->topo.ncomp * (s->cplx[1] ? 2 : 1) *
+                        esize(prec)) + 255) & ~(size_t)255;
+    W[1] = ws;
+    W[2] = (char*)ws + w1;
+  }
   for (Launch& L : s->passes) {
     PassParams p = L.p;
+    if (L.in_buf) p.in = W[L.in_buf];
+    if (L.out_buf) p.out = W[L.out_buf];
     if (L.user_in) p.in = rhs;
     if (L.user_out) p.out = phi;
     cudaError_t e = L.kind >= K_CURL_REAL ? launch_curl(L.kind, prec, p, L.grid, L.nthr, L.smem, st)
@@ -768,9 +794,65 @@ int flups_solve(flups_solver s, void* phi, const void* rhs, void* stream) {
   return FLUPS_OK;
 }
 
-int flups_solve_pass(flups_solver s, int i, void* phi, const void* rhs, void* stream) {
+int flups_solve(flups_solver s, void* phi, const void* rhs, void* stream) {
   if (!s || !phi || !rhs) return FLUPS_EINVAL;
   if (!s->ready) return FLUPS_ESTATE;
+  if (s->shared) return FLUPS_ESTATE;  // no own workspace: use flups_solve_ws
+  return solve_impl(s, phi, rhs, nullptr, stream);
+}
+
+int flups_solver_memory(flups_solver s, size_t* resident, size_t* transient, size_t* workspace) {
+  if (!s) return FLUPS_EINVAL;
+  const int prec = s->topo.prec, nc = s->topo.ncomp;
+  const size_t es = esize(prec);
+  size_t res = 0, tr = 0, ws = 0;
+  int du = 0;
+  size_t gn = 1, gmax = 0;
+  for (int d = 0; d < 3; ++d) {
+    res += (size_t)4 * s->dir[d].P * es;  // twiddles
+    du += s->dir[d].unb;
+    gn *= (size_t)s->dir[d].gext;
+    if ((size_t)s->dir[d].gext > gmax) gmax = s->dir[d].gext;
+    if (s->op == FLUPS_BIOT_SAVART) res += (size_t)s->dir[d].P * es;
+  }
+  if (du == 0) {
+    for (int d = 0; d < 3; ++d) res += (size_t)s->dir[d].gext * es;
+  } else {
+    res += gn * es;
+    tr += gn * sizeof(double) + (size_t)8 * 2 * gmax * sizeof(double);
+  }
+  for (int i = 1; i <= 2; ++i)
+    ws += (((size_t)s->dims[i][0] * s->dims[i][1] * s->dims[i][2] * nc * (s->cplx[i] ? 2 : 1) * es) + 255) & ~(size_t)255;
+  if (resident) *resident = res;
+  if (transient) *transient = tr;
+  if (workspace) *workspace = ws;
+  return FLUPS_OK;
+}
+
+int flups_workspace_size(flups_solver s, size_t* bytes) {
+  if (!s || !bytes) return FLUPS_EINVAL;
+  if (!s->ready) return FLUPS_ESTATE;
+  *bytes = s->ws_need;
+  return FLUPS_OK;
+}
+
+int flups_setup_shared(flups_solver s, void* stream) {
+  if (!s) return FLUPS_EINVAL;
+  if (s->ready) return s->shared ? FLUPS_OK : FLUPS_ESTATE;
+  s->shared = true;
+  return flups_setup(s, stream, nullptr);
+}
+
+int flups_solve_ws(flups_solver s, void* phi, const void* rhs, void* workspace, void* stream) {
+  if (!s || !phi || !rhs || !workspace) return FLUPS_EINVAL;
+  if (!s->ready) return FLUPS_ESTATE;
+  if (((uintptr_t)workspace & 255) != 0) return FLUPS_EINVAL;
+  return solve_impl(s, phi, rhs, workspace, stream);
+}
+
+int flups_solve_pass(flups_solver s, int i, void* phi, const void* rhs, void* stream) {
+  if (!s || !phi || !rhs) return FLUPS_EINVAL;
+  if (!s->ready || s->shared) return FLUPS_ESTATE;
   if (i < 0 || i >= (int)s->passes.size()) return FLUPS_EINVAL;
   const Launch& L = s->passes[i];
   PassParams p = L.p;
@@ -798,7 +880,7 @@ int flups_pass_info(flups_solver s, int i, int* kind, int* axis, int* fft_len, d
 
 int flups_solve_host(flups_solver s, void* phi_host, const void* rhs_host, void* stream) {
   if (!s || !phi_host || !rhs_host) return FLUPS_EINVAL;
-  if (!s->ready) return FLUPS_ESTATE;
+  if (!s->ready || s->shared) return FLUPS_ESTATE;
   cudaStream_t st = (cudaStream_t)stream;
   if (!s->stage) {
     cudaError_t e = cudaMalloc(&s->stage, s->user_bytes);

@@ -27,7 +27,23 @@ EXPORTED = (
     "flups_init_topo", "flups_topo_free", "flups_init_solver", "flups_setup", "flups_solve",
     "flups_solve_host", "flups_cleanup", "flups_solver_info", "flups_strerror", "flups_last_cuda_error",
     "flups_debug_special", "flups_solve_pass", "flups_pass_info", "flups_solve_periodic_noalloc",
+    "flups_setup_shared", "flups_workspace_size", "flups_solve_ws", "flups_solver_memory",
+    "flups_server_create", "flups_server_submit", "flups_server_poll", "flups_server_wait", "flups_server_pending",
+    "flups_server_get_stats", "flups_server_destroy",
 )
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("center", ctypes.c_int), ("prec", ctypes.c_int), ("op", ctypes.c_int),
+                ("diff", ctypes.c_int), ("bc", ctypes.c_int * 18), ("h", ctypes.c_double * 3),
+                ("L", ctypes.c_double * 3), ("green", ctypes.c_int), ("eps_over_h", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_longlong) for k in ("submitted", "admitted", "completed", "rejected", "failed",
+                                                   "queued_max", "plan_hits", "plan_misses", "slots_created",
+                                                   "evictions", "plans_cached")] + \
+               [("hbm_in_use", ctypes.c_size_t), ("hbm_peak", ctypes.c_size_t)]
 
 
 class FlupsError(RuntimeError):
@@ -66,6 +82,19 @@ def lib():
         L.flups_solve_pass.argtypes = [vp, ctypes.c_int, vp, vp, vp]
         L.flups_pass_info.argtypes = [vp, ctypes.c_int, ip, ip, ip, dp, dp]
         L.flups_solve_periodic_noalloc.argtypes = [vp, vp, ip, dp, vp]
+        szp = ctypes.POINTER(ctypes.c_size_t)
+        L.flups_setup_shared.argtypes = [vp, vp]
+        L.flups_workspace_size.argtypes = [vp, szp]
+        L.flups_solve_ws.argtypes = [vp, vp, vp, vp, vp]
+        L.flups_solver_memory.argtypes = [vp, szp, szp, szp]
+        llp = ctypes.POINTER(ctypes.c_longlong)
+        L.flups_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]
+        L.flups_server_submit.argtypes = [vp, ctypes.POINTER(Request), vp, vp, llp]
+        L.flups_server_poll.argtypes = [vp, llp, dp, ip, ctypes.c_int, ip]
+        L.flups_server_wait.argtypes = [vp, llp, dp, ip, ctypes.c_int, ip]
+        L.flups_server_pending.argtypes = [vp, ip, ip]
+        L.flups_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        L.flups_server_destroy.argtypes = [vp]
         for name in EXPORTED:
             if name not in ("flups_strerror", "flups_last_cuda_error"):
                 getattr(L, name).restype = ctypes.c_int
@@ -180,6 +209,97 @@ def flups_solve_periodic_noalloc(phi, rhs, n, L, stream=None):
     LL = (ctypes.c_double * 3)(*[float(v) for v in L])
     _check(lib().flups_solve_periodic_noalloc(_ptr(phi), _ptr(rhs), nn, LL, _stream(stream)),
            "flups_solve_periodic_noalloc")
+
+
+def flups_setup_shared(solver, stream=None):
+    _check(lib().flups_setup_shared(solver, _stream(stream)), "flups_setup_shared")
+
+
+def flups_workspace_size(solver) -> int:
+    b = ctypes.c_size_t(0)
+    _check(lib().flups_workspace_size(solver, ctypes.byref(b)), "flups_workspace_size")
+    return b.value
+
+
+def flups_solve_ws(solver, phi, rhs, workspace, stream=None):
+    _check(lib().flups_solve_ws(solver, _ptr(phi), _ptr(rhs), _ptr(workspace), _stream(stream)), "flups_solve_ws")
+
+
+def flups_solver_memory(solver):
+    r, t, w = ctypes.c_size_t(0), ctypes.c_size_t(0), ctypes.c_size_t(0)
+    _check(lib().flups_solver_memory(solver, ctypes.byref(r), ctypes.byref(t), ctypes.byref(w)),
+           "flups_solver_memory")
+    return {"resident": r.value, "transient": t.value, "workspace": w.value}
+
+
+def flups_server_create(hbm_budget_bytes, nstreams=8):
+    h = ctypes.c_void_p()
+    _check(lib().flups_server_create(int(hbm_budget_bytes), int(nstreams), ctypes.byref(h)), "flups_server_create")
+    return h
+
+
+def make_request(n, bc, center=CELL, prec=F64, op=POISSON, diff=DIFF_SPECTRAL, h=None, L=(1.0, 1.0, 1.0),
+                 green="spectral", eps_over_h=2.0):
+    r = Request()
+    r.n[:] = [int(v) for v in n]
+    r.center, r.prec, r.op, r.diff = int(center), int(prec), int(op), int(diff)
+    flat = []
+    if isinstance(bc[0][0], (list, tuple)):
+        for comp in bc:
+            for d in comp:
+                flat.extend(int(b) for b in d)
+    else:
+        for d in bc:
+            flat.extend(int(b) for b in d)
+    flat += [0] * (18 - len(flat))
+    r.bc[:] = flat
+    if h is None:
+        h = [L[d] / (n[d] if center == CELL else n[d] - 1) for d in range(3)]
+    r.h[:] = [float(v) for v in h]
+    r.L[:] = [float(v) for v in L]
+    r.green = KERNELS[green] if isinstance(green, str) else int(green)
+    r.eps_over_h = float(eps_over_h)
+    return r
+
+
+def flups_server_submit(server, request, rhs_host, phi_host):
+    t = ctypes.c_longlong(0)
+    _check(lib().flups_server_submit(server, ctypes.byref(request), _ptr(rhs_host), _ptr(phi_host), ctypes.byref(t)),
+           "flups_server_submit")
+    return t.value
+
+
+def _server_done(fn, server, maxn):
+    tk = (ctypes.c_longlong * maxn)()
+    lat = (ctypes.c_double * maxn)()
+    st = (ctypes.c_int * maxn)()
+    n = ctypes.c_int(0)
+    _check(fn(server, tk, lat, st, maxn, ctypes.byref(n)), fn.__name__)
+    return [(tk[i], lat[i], st[i]) for i in range(n.value)]
+
+
+def flups_server_poll(server, maxn=1024):
+    return _server_done(lib().flups_server_poll, server, maxn)
+
+
+def flups_server_wait(server, maxn=1024):
+    return _server_done(lib().flups_server_wait, server, maxn)
+
+
+def flups_server_pending(server):
+    q, r = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().flups_server_pending(server, ctypes.byref(q), ctypes.byref(r)), "flups_server_pending")
+    return q.value, r.value
+
+
+def flups_server_get_stats(server):
+    st = ServerStats()
+    _check(lib().flups_server_get_stats(server, ctypes.byref(st)), "flups_server_get_stats")
+    return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+
+def flups_server_destroy(server):
+    _check(lib().flups_server_destroy(server), "flups_server_destroy")
 
 
 def flups_debug_special(which, x, y, out, n, eps):
