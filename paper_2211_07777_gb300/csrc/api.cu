@@ -9,6 +9,7 @@
 // forward transform, multiplication by G^ (eq. poisson), inverse transform.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -288,10 +289,19 @@ void fill_geom(Launch& L, const DirPlan& dp, int axis, const int* din, const int
   p.axis = axis;
   p.npen = axis == 0 ? din[1] * din[2] : din[0];
   int W, nthr;
-  tile_shape(dp.P, prec, p.npen, packed, &W, &nthr, share);
+  const int wct = share == 1 ? ct_tile_width(dp.P, prec) : 0;  // the curl pass keeps the runtime engine
+  if (wct) {
+    W = wct;
+    nthr = dp.P * W / 16;
+    p.ct = 1;
+    p.LS = W + 1;
+  } else {
+    tile_shape(dp.P, prec, p.npen, packed, &W, &nthr, share);
+    p.ct = 0;
+    p.LS = (axis == 0 && W >= 8) ? W + 1 : W;
+  }
   p.W = W;
   p.lw = ilog2(W);
-  p.LS = (axis == 0 && W >= 8) ? W + 1 : W;
   p.type = dp.type;
   p.ctypes = dp.type | (dp.type << 4) | (dp.type << 8);
   p.center = center;
@@ -300,12 +310,17 @@ void fill_geom(Launch& L, const DirPlan& dp, int axis, const int* din, const int
   p.P = dp.P;
   p.n_modes = dp.nm;
   p.n_use = (dp.type == T_PER) ? dp.N : dp.n_data;
+  {
+    int m = std::max(std::max(p.n_data, p.n_use), p.n_modes);
+    p.ndlog = ilog2(m);
+    p.hlog = ilog2(dp.P / 2 + 1);
+  }
   p.plan = dp.rp;
   p.tw = dp.tw;
   const int per_tile = packed ? 2 * W : W;
   L.grid = dim3((p.npen + per_tile - 1) / per_tile, axis == 0 ? 1 : (axis == 1 ? din[2] : din[1]), ncomp);
   L.nthr = nthr;
-  L.smem = 2 * (size_t)dp.P * p.LS * 2 * esize(prec) + 16 * 2 * W + 16;
+  L.smem = (p.ct ? 1 : 2) * (size_t)dp.P * p.LS * 2 * esize(prec) + 16 * 2 * W + 16;
 }
 
 int setup_green(flups_solver_s* s, cudaStream_t st) {

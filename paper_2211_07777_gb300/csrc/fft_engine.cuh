@@ -206,4 +206,88 @@ __device__ __forceinline__ cpx<T>* fft_tile(cpx<T>* A, cpx<T>* B, int LS, int P,
   return X;
 }
 
+// ---------------------------------------------------------------------------
+// Compile-time tile engine for P = 2^a: every stage's radix, stride and
+// twiddle step, the tile width W and the block size NT = P W / 16 are known
+// at compile time, so the index arithmetic folds to shifts and masks.  The
+// tile is transformed in place in one buffer: every thread reads its 16
+// elements of a stage into registers, the block synchronises, and the thread
+// writes them back (16 = the elements of one radix-16 butterfly, of two
+// radix-8 or four radix-4 butterflies).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int ct_radix(int rem) {
+  // remaining length rem = 2^a: 16s first, a remainder of 32 as 8 x 4, then 8, 4, 2
+  return rem == 32 ? 8 : (rem >= 16 ? 16 : rem);
+}
+
+template <typename T, int P, int W, int NT, int R, int Ns, bool INV>
+__device__ __forceinline__ void ct_stage(cpx<T>* S, const cpx<T>* __restrict__ tw, int tid) {
+  constexpr int LS = W + 1;
+  constexpr int nbf = P / R;
+  constexpr int NB = (nbf * W) / NT;
+  static_assert((nbf * W) % NT == 0, "tile and block do not match");
+  constexpr int tstep = (2 * P) / (Ns * R);
+  cpx<T> v[NB][R];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int idx = tid + b * NT;
+    const int lane = idx % W, j = idx / W, k = j % Ns;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[b][r] = S[(j + r * nbf) * LS + lane];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const cpx<T> w = __ldg(&tw[r * k * tstep]);
+        v[b][r] = INV ? cmulc<T>(v[b][r], w) : cmul<T>(v[b][r], w);
+      }
+    }
+    dftR<T, R, INV>(v[b]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int idx = tid + b * NT;
+    const int lane = idx % W, j = idx / W, k = j % Ns;
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) S[(base + r * Ns) * LS + lane] = v[b][r];
+  }
+  __syncthreads();
+}
+
+template <typename T, int P, int W, int NT, int Ns, bool INV>
+__device__ __forceinline__ void ct_stages(cpx<T>* S, const cpx<T>* __restrict__ tw, int tid) {
+  if constexpr (Ns < P) {
+    constexpr int R = ct_radix(P / Ns);
+    ct_stage<T, P, W, NT, R, Ns, INV>(S, tw, tid);
+    ct_stages<T, P, W, NT, Ns * R, INV>(S, tw, tid);
+  }
+}
+
+// Stage s of the compile-time plan (forward order): number of stages, radix, Ns.
+__host__ __device__ constexpr int ct_nstages(int P) {
+  int n = 0, ns = 1;
+  while (ns < P) { ns *= ct_radix(P / ns); ++n; }
+  return n;
+}
+__host__ __device__ constexpr int ct_ns(int P, int s) {
+  int ns = 1;
+  for (int i = 0; i < s; ++i) ns *= ct_radix(P / ns);
+  return ns;
+}
+__host__ __device__ constexpr int ct_rad(int P, int s) { return ct_radix(P / ct_ns(P, s)); }
+// the same plan run in reverse radix order (inverse transform of the fused pass)
+__host__ __device__ constexpr int ct_rad_rev(int P, int s) { return ct_rad(P, ct_nstages(P) - 1 - s); }
+__host__ __device__ constexpr int ct_ns_rev(int P, int s) {
+  int ns = 1;
+  for (int i = 0; i < s; ++i) ns *= ct_rad_rev(P, i);
+  return ns;
+}
+
+// In-place transform of the tile in S (lane stride W + 1); ends with a barrier.
+template <typename T, int P, int W, bool INV>
+__device__ __forceinline__ void fft_tile_ct(cpx<T>* S, const cpx<T>* __restrict__ tw, int tid) {
+  ct_stages<T, P, W, P * W / 16, 1, INV>(S, tw, tid);
+}
+
 }  // namespace flups

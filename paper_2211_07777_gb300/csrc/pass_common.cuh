@@ -8,9 +8,6 @@ namespace flups {
 // Transform type of component `comp` (4 bits per component).
 __device__ __forceinline__ int comp_type(const PassParams& p, int comp) { return (p.ctypes >> (4 * comp)) & 15; }
 
-// Largest block the planner launches: 512 threads (FP32) and 256 (FP64).
-template <typename T> struct MaxThreads { static constexpr int value = 512; };
-template <> struct MaxThreads<double> { static constexpr int value = 256; };
 
 // ---------------------------------------------------------------------------
 // Extension geometry (Sections 2.2, 2.3).  Data index i (already mirrored for
@@ -102,19 +99,20 @@ __device__ __forceinline__ int primary_pos(int t, int center, int N, int i) {
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void zero_fill(cpx<T>* S, int LS, int W, int lo, int hi, int tid, int nthr) {
+  // W is a power of two
   const int tot = (hi - lo) * W;
   for (int idx = tid; idx < tot; idx += nthr) {
-    const int lane = idx % W;
+    const int lane = idx & (W - 1);
     const int j = lo + idx / W;
     S[j * LS + lane] = mk<T>((T)0, (T)0);
   }
 }
 
 // Build the two-pencil extension of real data (pencils q0 + c, c < 2W).
-template <typename T>
+template <typename T, int WC = 0>
 __device__ __forceinline__ void load_real_ext(const PassParams& p, int type, const T* __restrict__ in, cpx<T>* S,
                                               int q0, int tid, int nthr) {
-  const int W = p.W, LS = p.LS, N = p.N, nd = p.n_data;
+  const int W = WC ? WC : p.W, LS = WC ? WC + 1 : p.LS, N = p.N, nd = p.n_data;
   const int t = base_type(type);
   const bool rev = is_reversed(type);
   int lo[3], hi[3];
@@ -122,11 +120,13 @@ __device__ __forceinline__ void load_real_ext(const PassParams& p, int type, con
   for (int r = 0; r < nz; ++r) zero_fill<T>(S, LS, W, lo[r], hi[r], tid, nthr);
   T* Sr = reinterpret_cast<T*>(S);
   const int W2 = 2 * W;
-  const int tot = nd * W2;
   const bool rowmode = p.axis == 0;
+  // row mode: index i fastest over a power-of-two stride (1 << ndlog) >= nd
+  const int tot = rowmode ? (W2 << p.ndlog) : nd * W2;
   for (int idx = tid; idx < tot; idx += nthr) {
     int c, i;
-    if (rowmode) { i = idx % nd; c = idx / nd; } else { c = idx % W2; i = idx / W2; }
+    if (rowmode) { i = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (i >= nd) continue; }
+    else { c = idx & (W2 - 1); i = idx / W2; }
     const int q = q0 + c;
     T v = (T)0;
     if (q < p.npen) v = in[(long long)q * p.ai.ls + (long long)i * p.ai.js];
@@ -139,25 +139,26 @@ __device__ __forceinline__ void load_real_ext(const PassParams& p, int type, con
 }
 
 // Store data values of both pencils of every lane from the inverse-transformed extension.
-template <typename T>
+template <typename T, int WC = 0>
 __device__ __forceinline__ void store_real_data(const PassParams& p, int type, T* __restrict__ out, const cpx<T>* S,
                                                 int q0, int tid, int nthr) {
-  const int W = p.W, N = p.N, nd = p.n_data;
+  const int W = WC ? WC : p.W, LS = WC ? WC + 1 : p.LS, N = p.N, nd = p.n_data;
   const int t = base_type(type);
   const bool rev = is_reversed(type);
   const int W2 = 2 * W;
-  const int tot = nd * W2;
   const bool rowmode = p.axis == 0;
+  const int tot = rowmode ? (W2 << p.ndlog) : nd * W2;
   for (int idx = tid; idx < tot; idx += nthr) {
     int c, i;
-    if (rowmode) { i = idx % nd; c = idx / nd; } else { c = idx % W2; i = idx / W2; }
+    if (rowmode) { i = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (i >= nd) continue; }
+    else { c = idx & (W2 - 1); i = idx / W2; }
     const int q = q0 + c;
     if (q >= p.npen) continue;
     const int ii = rev ? nd - 1 - i : i;
     const int pos = primary_pos(t, p.center, N, ii);
     T v = (T)0;
     if (pos >= 0) {
-      const cpx<T> z = S[pos * p.LS + (c >> 1)];
+      const cpx<T> z = S[pos * LS + (c >> 1)];
       v = (c & 1) ? z.y : z.x;
     }
     out[(long long)q * p.ao.ls + (long long)i * p.ao.js] = v;
@@ -172,16 +173,17 @@ __device__ __forceinline__ cpx<T> split(cpx<T> zk, cpx<T> zm, int part) {
 }
 
 
-template <typename T>
+template <typename T, int WC = 0>
 __device__ __forceinline__ void load_cplx(const PassParams& p, const cpx<T>* __restrict__ in, cpx<T>* S, int q0,
                                           int tid, int nthr) {
-  const int W = p.W, LS = p.LS, nu = p.n_use;
+  const int W = WC ? WC : p.W, LS = WC ? WC + 1 : p.LS, nu = p.n_use;
   if (nu < p.P) zero_fill<T>(S, LS, W, nu, p.P, tid, nthr);
-  const int tot = nu * W;
   const bool rowmode = p.axis == 0;
+  const int tot = rowmode ? (W << p.ndlog) : nu * W;
   for (int idx = tid; idx < tot; idx += nthr) {
     int lane, i;
-    if (rowmode) { i = idx % nu; lane = idx / nu; } else { lane = idx % W; i = idx / W; }
+    if (rowmode) { i = idx & ((1 << p.ndlog) - 1); lane = idx >> p.ndlog; if (i >= nu) continue; }
+    else { lane = idx & (W - 1); i = idx / W; }
     const int q = q0 + lane;
     cpx<T> v = mk<T>((T)0, (T)0);
     if (q < p.npen) v = in[(long long)q * p.ai.ls + (long long)i * p.ai.js];
@@ -189,15 +191,16 @@ __device__ __forceinline__ void load_cplx(const PassParams& p, const cpx<T>* __r
   }
 }
 
-template <typename T>
+template <typename T, int WC = 0>
 __device__ __forceinline__ void store_cplx_data(const PassParams& p, cpx<T>* __restrict__ out, const cpx<T>* S, int q0,
                                                 int tid, int nthr) {
-  const int W = p.W, LS = p.LS, nd = p.n_data;
-  const int tot = nd * W;
+  const int W = WC ? WC : p.W, LS = WC ? WC + 1 : p.LS, nd = p.n_data;
   const bool rowmode = p.axis == 0;
+  const int tot = rowmode ? (W << p.ndlog) : nd * W;
   for (int idx = tid; idx < tot; idx += nthr) {
     int lane, i;
-    if (rowmode) { i = idx % nd; lane = idx / nd; } else { lane = idx % W; i = idx / W; }
+    if (rowmode) { i = idx & ((1 << p.ndlog) - 1); lane = idx >> p.ndlog; if (i >= nd) continue; }
+    else { lane = idx & (W - 1); i = idx / W; }
     const int q = q0 + lane;
     if (q >= p.npen) continue;
     const int pos = (p.type == T_PER && p.center == C_NODE && i == p.N) ? 0 : i;

@@ -1,0 +1,572 @@
+// Pass kernels of the solve, as templates over the arithmetic type T and the
+// tile shape: PC = 0 takes the FFT length and tile width from the parameters
+// (runtime engine, any P = 2^a 3^b, ping-pong buffers); PC = P > 0 compiles
+// the whole tile for P = 2^a and WC lanes (compile-time engine, in place).
+//
+// Every pass moves a tile of pencils through shared memory: gather from HBM
+// (coalesced along x), build the periodic extension in shared memory (zero
+// padding and symmetric images are never stored in HBM), complex FFT of the
+// extension, then either store modes or -- in the fused last direction --
+// multiply by the Green's function spectrum and transform back.
+//
+// Real data are always transformed two pencils at a time: pencil a in the real
+// part and pencil b in the imaginary part of one complex sequence, separated
+// after the FFT through Hermitian symmetry (A_k = (Z_k + conj Z_{P-k})/2,
+// B_k = (Z_k - conj Z_{P-k})/(2i)).  This serves the R2C DFT (Section 2.2,
+// eq. sec2_dft_def) and the DCT/DST types I-IV of Table 1 alike: each r2r
+// transform is read off the DFT of its even/odd extension, with the
+// half-sample phase exp(-i pi k/P) for cell-centred data.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "pass_common.cuh"
+#include "passes.cuh"
+
+namespace flups {
+
+// Launch bounds: the runtime engine runs at most 512 (FP32) / 256 (FP64)
+// threads; the compile-time engine exactly P W / 16.
+template <typename T, int PC, int WC> struct KBounds {
+  static constexpr int threads = PC ? PC * WC / 16 : (sizeof(T) == 4 ? 512 : 256);
+  static constexpr int minb = PC ? ((sizeof(T) == 4 ? 1024 : 512) / threads > 0 ? (sizeof(T) == 4 ? 1024 : 512) / threads : 1) : 1;
+};
+
+template <typename T, int PC, int WC>
+struct Tile {
+  static constexpr bool CT = PC > 0;
+  __device__ __forceinline__ static int P(const PassParams& p) { return CT ? PC : p.P; }
+  __device__ __forceinline__ static int W(const PassParams& p) { return CT ? WC : p.W; }
+  __device__ __forceinline__ static int LS(const PassParams& p) { return CT ? WC + 1 : p.LS; }
+};
+
+// FFT of the tile held in S (S2 = second buffer of the runtime engine); returns the buffer holding the result.
+template <typename T, int PC, int WC, bool INV>
+__device__ __forceinline__ cpx<T>* run_fft(const PassParams& p, cpx<T>* S, cpx<T>* S2, const cpx<T>* tw, int tid,
+                                           int nthr) {
+  if constexpr (PC > 0) {
+    fft_tile_ct<T, PC, WC, INV>(S, tw, tid);
+    return S;
+  } else {
+    return fft_tile<T, INV>(S, S2, p.LS, p.P, p.W, p.lw, p.plan, tw, tid, nthr);
+  }
+}
+
+template <typename T, int PC>
+__device__ __forceinline__ cpx<T>* second_buffer(const PassParams& p, cpx<T>* S) {
+  return PC > 0 ? S : S + (size_t)p.P * p.LS;
+}
+
+// Spectrum value X_kk of one pencil rebuilt from its stored modes (inverse of the forward store).
+template <typename T>
+__device__ __forceinline__ cpx<T> stored_mode(const PassParams& p, int type, const void* in, long long off_pencil,
+                                              int kk, int P, const cpx<T>* tw) {
+  const int t = base_type(type);
+  if (t == T_PER || t == T_UNB) {
+    cpx<T> X = ((const cpx<T>*)in)[off_pencil + (long long)kk * p.ai.js];
+    if (kk == 0 || 2 * kk == P) X.y = (T)0;  // DC and Nyquist of a real signal are real
+    return X;
+  }
+  int m = kk;
+  T div = (T)1;
+  if (is_quarter(t)) {
+    if ((kk & 1) == 0) return mk<T>((T)0, (T)0);
+    m = (kk - 1) >> 1;
+    div = (T)2;
+  }
+  const T c = ((const T*)in)[off_pencil + (long long)m * p.ai.js] * div;
+  cpx<T> F = is_odd_origin(t) ? mk<T>((T)0, -c) : mk<T>(c, (T)0);
+  if (p.center == C_CELL) F = cmulc<T>(F, __ldg(&tw[kk]));
+  return F;
+}
+
+// ---------------------------------------------------------------------------
+// Forward pass on real data: R2C (periodic, doubled unbounded) or r2r
+// coefficients (symmetric and semi-unbounded directions).
+// ---------------------------------------------------------------------------
+template <typename T, int PC, int WC>
+__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fwd_real(PassParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  using TL = Tile<T, PC, WC>;
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int W = TL::W(p), LS = TL::LS(p), P = TL::P(p);
+  const int q0 = blockIdx.x * 2 * W;
+  const long long obase_i = (long long)blockIdx.y * p.ai.os + (long long)blockIdx.z * p.ai.cs;
+  const long long obase_o = (long long)blockIdx.y * p.ao.os + (long long)blockIdx.z * p.ao.cs;
+  const int ctype = comp_type(p, blockIdx.z);
+  load_real_ext<T, WC>(p, ctype, (const T*)p.in + obase_i, S, q0, tid, nthr);
+  __syncthreads();
+  const cpx<T>* tw = (const cpx<T>*)p.tw;
+  S = run_fft<T, PC, WC, false>(p, S, second_buffer<T, PC>(p, S), tw, tid, nthr);
+
+  const int t = base_type(ctype);
+  const bool cplx_out = (t == T_PER || t == T_UNB);
+  const bool quarter = is_quarter(t);
+  const bool oddo = is_odd_origin(t);
+  const bool cell = p.center == C_CELL;
+  const int W2 = 2 * W, nm = p.n_modes;
+  const bool rowmode = p.axis == 0;
+  const int tot = rowmode ? (W2 << p.ndlog) : nm * W2;
+  for (int idx = tid; idx < tot; idx += nthr) {
+    int c, k;
+    if (rowmode) { k = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (k >= nm) continue; }
+    else { c = idx & (W2 - 1); k = idx / W2; }
+    const int q = q0 + c;
+    if (q >= p.npen) continue;
+    const int lane = c >> 1, part = c & 1;
+    const int kk = quarter ? 2 * k + 1 : k;
+    const int km = kk == 0 ? 0 : P - kk;
+    const cpx<T> X = split<T>(S[kk * LS + lane], S[km * LS + lane], part);
+    const long long off = (long long)q * p.ao.ls + (long long)k * p.ao.js;
+    if (cplx_out) {
+      ((cpx<T>*)p.out)[obase_o + off] = X;
+    } else {
+      cpx<T> F = X;
+      if (cell) F = cmul<T>(X, __ldg(&tw[kk]));
+      T v = oddo ? -F.y : F.x;
+      if (quarter) v *= (T)0.5;
+      ((T*)p.out)[obase_o + off] = v;
+    }
+  }
+}
+
+template <typename T, int PC, int WC>
+__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_inv_real(PassParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  using TL = Tile<T, PC, WC>;
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int W = TL::W(p), LS = TL::LS(p), P = TL::P(p);
+  const int q0 = blockIdx.x * 2 * W;
+  const long long obase_i = (long long)blockIdx.y * p.ai.os + (long long)blockIdx.z * p.ai.cs;
+  const long long obase_o = (long long)blockIdx.y * p.ao.os + (long long)blockIdx.z * p.ao.cs;
+  const cpx<T>* tw = (const cpx<T>*)p.tw;
+  const int ctype = comp_type(p, blockIdx.z);
+  const int half = P / 2;
+  const bool rowmode = p.axis == 0;
+  // row mode: k fastest over a power-of-two stride (1 << p.hlog) >= half + 1
+  const int tot = rowmode ? (W << p.hlog) : (half + 1) * W;
+  for (int idx = tid; idx < tot; idx += nthr) {
+    int lane, k;
+    if (rowmode) { k = idx & ((1 << p.hlog) - 1); lane = idx >> p.hlog; if (k > half) continue; }
+    else { lane = idx & (W - 1); k = idx / W; }
+    const int qa = q0 + 2 * lane, qb = qa + 1;
+    cpx<T> Xa = mk<T>((T)0, (T)0), Xb = Xa;
+    if (qa < p.npen) Xa = stored_mode<T>(p, ctype, p.in, obase_i + (long long)qa * p.ai.ls, k, P, tw);
+    if (qb < p.npen) Xb = stored_mode<T>(p, ctype, p.in, obase_i + (long long)qb * p.ai.ls, k, P, tw);
+    S[k * LS + lane] = mk<T>(Xa.x - Xb.y, Xa.y + Xb.x);
+    if (k != 0 && 2 * k != P) S[(P - k) * LS + lane] = mk<T>(Xa.x + Xb.y, Xb.x - Xa.y);
+  }
+  __syncthreads();
+  S = run_fft<T, PC, WC, true>(p, S, second_buffer<T, PC>(p, S), tw, tid, nthr);
+  store_real_data<T, WC>(p, ctype, (T*)p.out + obase_o, S, q0, tid, nthr);
+}
+
+// ---------------------------------------------------------------------------
+// Complex passes (second and third complex directions).
+// ---------------------------------------------------------------------------
+template <typename T, int PC, int WC>
+__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fwd_c2c(PassParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  using TL = Tile<T, PC, WC>;
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int W = TL::W(p), LS = TL::LS(p), P = TL::P(p);
+  const int q0 = blockIdx.x * W;
+  const long long obase_i = (long long)blockIdx.y * p.ai.os + (long long)blockIdx.z * p.ai.cs;
+  const long long obase_o = (long long)blockIdx.y * p.ao.os + (long long)blockIdx.z * p.ao.cs;
+  load_cplx<T, WC>(p, (const cpx<T>*)p.in + obase_i, S, q0, tid, nthr);
+  __syncthreads();
+  S = run_fft<T, PC, WC, false>(p, S, second_buffer<T, PC>(p, S), (const cpx<T>*)p.tw, tid, nthr);
+  cpx<T>* out = (cpx<T>*)p.out + obase_o;
+  const bool rowmode = p.axis == 0;
+  const int tot = P * W;
+  for (int idx = tid; idx < tot; idx += nthr) {
+    int lane, k;
+    if (rowmode) { k = idx % P; lane = idx / P; } else { lane = idx & (W - 1); k = idx / W; }
+    const int q = q0 + lane;
+    if (q >= p.npen) continue;
+    out[(long long)q * p.ao.ls + (long long)k * p.ao.js] = S[k * LS + lane];
+  }
+}
+
+template <typename T, int PC, int WC>
+__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_inv_c2c(PassParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  using TL = Tile<T, PC, WC>;
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int W = TL::W(p), LS = TL::LS(p), P = TL::P(p);
+  const int q0 = blockIdx.x * W;
+  const long long obase_i = (long long)blockIdx.y * p.ai.os + (long long)blockIdx.z * p.ai.cs;
+  const long long obase_o = (long long)blockIdx.y * p.ao.os + (long long)blockIdx.z * p.ao.cs;
+  const cpx<T>* in = (const cpx<T>*)p.in + obase_i;
+  const bool rowmode = p.axis == 0;
+  const int tot = P * W;
+  for (int idx = tid; idx < tot; idx += nthr) {
+    int lane, k;
+    if (rowmode) { k = idx % P; lane = idx / P; } else { lane = idx & (W - 1); k = idx / W; }
+    const int q = q0 + lane;
+    cpx<T> v = mk<T>((T)0, (T)0);
+    if (q < p.npen) v = in[(long long)q * p.ai.ls + (long long)k * p.ai.js];
+    S[k * LS + lane] = v;
+  }
+  __syncthreads();
+  S = run_fft<T, PC, WC, true>(p, S, second_buffer<T, PC>(p, S), (const cpx<T>*)p.tw, tid, nthr);
+  store_cplx_data<T, WC>(p, (cpx<T>*)p.out + obase_o, S, q0, tid, nthr);
+}
+
+// ---------------------------------------------------------------------------
+// Fused last direction: forward FFT, times G^, inverse FFT (u^ = G^ f^, eq. poisson).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T green_closed(int kernel, T k2, T eps2h, T scale) {
+  if (!(k2 > (T)0)) return (T)0;
+  if (kernel == 0 || kernel == 100) return -scale / k2;
+  const int m = kernel / 2;
+  const T s = k2 * eps2h;
+  T acc = (T)1, term = (T)1;
+  for (int j = 1; j < m; ++j) {
+    term = term * s / (T)j;
+    acc += term;
+  }
+  return -scale * exp(-s) * acc / k2;
+}
+
+// Green index of a pencil along the two non-axis directions: stored offset
+// (without the axis term) or the closed-form partial |k|^2.
+template <typename T>
+__device__ __forceinline__ void pencil_green_base(const PassParams& p, int q, int o, long long* goff, T* k2p) {
+  const FusedGreen& g = p.g;
+  if (q >= p.npen) {  // ragged tile: no pencil, no Green access
+    *goff = 0;
+    *k2p = (T)0;
+    return;
+  }
+  int c[3];
+  if (p.axis == 0) { c[1] = q % g.dims1; c[2] = q / g.dims1; c[0] = 0; }
+  else if (p.axis == 1) { c[0] = q; c[2] = o; c[1] = 0; }
+  else { c[0] = q; c[1] = o; c[2] = 0; }
+  long long off = 0;
+  T k2 = (T)0;
+  const long long st[3] = {1, (long long)g.gext[0], (long long)g.gext[0] * g.gext[1]};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (d == p.axis) continue;
+    int gi = c[d];
+    if (g.fold[d]) gi = min(gi, g.fold[d] - gi);
+    off += gi * st[d];
+    if (!g.stored) k2 += ((const T*)g.tab[d])[gi];
+  }
+  *goff = off;
+  *k2p = k2;
+}
+
+template <typename T>
+__device__ __forceinline__ T green_at(const PassParams& p, long long goff, T k2p, int g3) {
+  const FusedGreen& g = p.g;
+  if (g.stored) {
+    const long long st3 = p.axis == 0 ? 1 : (p.axis == 1 ? (long long)g.gext[0] : (long long)g.gext[0] * g.gext[1]);
+    return __ldg(&((const T*)g.stored)[goff + g3 * st3]);
+  }
+  const T k2 = k2p + ((const T*)g.tab[p.axis])[g3];
+  return green_closed<T>(g.kernel, k2, (T)g.eps2_half, (T)g.scale);
+}
+
+template <typename T, int PC>
+__device__ __forceinline__ size_t tile_bytes(const PassParams& p) {
+  return (PC > 0 ? 1 : 2) * (size_t)p.P * p.LS * sizeof(cpx<T>);
+}
+
+template <typename T, int PC, int WC>
+__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fused_c2c(PassParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  using TL = Tile<T, PC, WC>;
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int W = TL::W(p), LS = TL::LS(p), P = TL::P(p);
+  cpx<T>* S2 = second_buffer<T, PC>(p, S);
+  long long* goff = reinterpret_cast<long long*>(smraw + tile_bytes<T, PC>(p));
+  T* k2p = reinterpret_cast<T*>(goff + W);
+  const int q0 = blockIdx.x * W;
+  const long long obase = (long long)blockIdx.y * p.ai.os + (long long)blockIdx.z * p.ai.cs;
+  for (int lane = tid; lane < W; lane += nthr) pencil_green_base<T>(p, q0 + lane, blockIdx.y, &goff[lane], &k2p[lane]);
+  load_cplx<T, WC>(p, (const cpx<T>*)p.in + obase, S, q0, tid, nthr);
+  __syncthreads();
+  const cpx<T>* tw = (const cpx<T>*)p.tw;
+  cpx<T>* X = run_fft<T, PC, WC, false>(p, S, S2, tw, tid, nthr);
+  const int tot = P * W;
+  for (int idx = tid; idx < tot; idx += nthr) {
+    const int lane = idx & (W - 1), k = idx / W;
+    const int g3 = min(k, P - k);
+    const T G = green_at<T>(p, goff[lane], k2p[lane], g3);
+    X[k * LS + lane] = cscale<T>(X[k * LS + lane], G);
+  }
+  __syncthreads();
+  X = run_fft<T, PC, WC, true>(p, X, X == S ? S2 : S, tw, tid, nthr);
+  store_cplx_data<T, WC>(p, (cpx<T>*)p.out + obase, X, q0, tid, nthr);
+}
+
+template <typename T, int PC, int WC>
+__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fused_real(PassParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  using TL = Tile<T, PC, WC>;
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int W = TL::W(p), LS = TL::LS(p), P = TL::P(p);
+  cpx<T>* S2 = second_buffer<T, PC>(p, S);
+  long long* goff = reinterpret_cast<long long*>(smraw + tile_bytes<T, PC>(p));
+  T* k2p = reinterpret_cast<T*>(goff + 2 * W);
+  const int q0 = blockIdx.x * 2 * W;
+  const long long obase = (long long)blockIdx.y * p.ai.os + (long long)blockIdx.z * p.ai.cs;
+  for (int c = tid; c < 2 * W; c += nthr) pencil_green_base<T>(p, q0 + c, blockIdx.y, &goff[c], &k2p[c]);
+  const int ctype = comp_type(p, blockIdx.z);
+  load_real_ext<T, WC>(p, ctype, (const T*)p.in + obase, S, q0, tid, nthr);
+  __syncthreads();
+  const cpx<T>* tw = (const cpx<T>*)p.tw;
+  cpx<T>* X = run_fft<T, PC, WC, false>(p, S, S2, tw, tid, nthr);
+  const bool quarter = is_quarter(base_type(ctype));
+  const int half = P / 2;
+  const int tot = (half + 1) * W;
+  for (int idx = tid; idx < tot; idx += nthr) {
+    const int lane = idx & (W - 1), k = idx / W;
+    const int km = k == 0 ? 0 : P - k;
+    const cpx<T> zk = X[k * LS + lane], zm = X[km * LS + lane];
+    cpx<T> A = split<T>(zk, zm, 0), B = split<T>(zk, zm, 1);
+    if (quarter && (k & 1) == 0) {
+      A = mk<T>((T)0, (T)0);
+      B = A;
+    } else {
+      const int g3 = quarter ? (k - 1) >> 1 : k;
+      const T Ga = green_at<T>(p, goff[2 * lane], k2p[2 * lane], g3);
+      const T Gb = green_at<T>(p, goff[2 * lane + 1], k2p[2 * lane + 1], g3);
+      A = cscale<T>(A, Ga);
+      B = cscale<T>(B, Gb);
+    }
+    X[k * LS + lane] = mk<T>(A.x - B.y, A.y + B.x);
+    if (k != 0 && 2 * k != P) X[km * LS + lane] = mk<T>(A.x + B.y, B.x - A.y);
+  }
+  __syncthreads();
+  X = run_fft<T, PC, WC, true>(p, X, X == S ? S2 : S, tw, tid, nthr);
+  store_real_data<T, WC>(p, ctype, (T*)p.out + obase, X, q0, tid, nthr);
+}
+
+// ---------------------------------------------------------------------------
+// Column-mode compile-time kernels (complex passes along y or z): the first
+// stage reads its butterfly inputs straight from HBM into registers (loads
+// coalesced across the W lanes = consecutive x), the last stage stores
+// straight from registers to HBM, and the fused pass keeps the last forward
+// stage's outputs in registers, multiplies them by G^ and runs the first
+// inverse stage on them -- the inverse plan takes the radices in reverse
+// order so that its first butterflies read exactly those elements.  Shared
+// memory carries only the exchanges between stages.
+// ---------------------------------------------------------------------------
+enum XsMode : int { XS_SMEM = 0, XS_GLOBAL = 1, XS_REGS = 2 };
+
+template <typename T>
+struct ColIO {
+  const cpx<T>* in;
+  cpx<T>* out;
+  long long ils, ijs, ols, ojs;
+  int q0, npen;
+  int n_in, n_out;  // rows read (the rest is zero padding) and rows written (truncation)
+  int dup;          // node-centred periodic: index 0 is also written to index dup (else -1)
+};
+
+template <typename T, int P, int W, int NT, int R, int Ns, bool INV, int SRC, int DST>
+__device__ __forceinline__ void xstage(cpx<T>* S, cpx<T>* v, const cpx<T>* __restrict__ tw, int tid,
+                                       const ColIO<T>& io) {
+  constexpr int LS = W + 1;
+  constexpr int nbf = P / R;
+  constexpr int NB = (nbf * W) / NT;
+  static_assert(NB * R == 16, "16 elements per thread");
+  constexpr int tstep = (2 * P) / (Ns * R);
+  if constexpr (SRC != XS_REGS) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int idx = tid + b * NT;
+      const int lane = idx % W, j = idx / W;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int i = j + r * nbf;
+        if constexpr (SRC == XS_SMEM) {
+          v[b * R + r] = S[i * LS + lane];
+        } else {
+          const int q = io.q0 + lane;
+          v[b * R + r] = (q < io.npen && i < io.n_in) ? io.in[(long long)q * io.ils + (long long)i * io.ijs]
+                                                      : mk<T>((T)0, (T)0);
+        }
+      }
+    }
+    if constexpr (SRC == XS_SMEM) __syncthreads();
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int idx = tid + b * NT;
+    const int j = idx / W, k = j % Ns;
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const cpx<T> w = __ldg(&tw[r * k * tstep]);
+        v[b * R + r] = INV ? cmulc<T>(v[b * R + r], w) : cmul<T>(v[b * R + r], w);
+      }
+    }
+    dftR<T, R, INV>(&v[b * R]);
+  }
+  if constexpr (DST != XS_REGS) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int idx = tid + b * NT;
+      const int lane = idx % W, j = idx / W, k = j % Ns;
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int o = base + r * Ns;
+        if constexpr (DST == XS_SMEM) {
+          S[o * LS + lane] = v[b * R + r];
+        } else {
+          const int q = io.q0 + lane;
+          if (q < io.npen) {
+            if (o < io.n_out) io.out[(long long)q * io.ols + (long long)o * io.ojs] = v[b * R + r];
+            if (o == 0 && io.dup >= 0) io.out[(long long)q * io.ols + (long long)io.dup * io.ojs] = v[b * R + r];
+          }
+        }
+      }
+    }
+    if constexpr (DST == XS_SMEM) __syncthreads();
+  }
+}
+
+template <typename T, int P, int W, bool INV, bool REV, int s, int SRC0, int DSTL>
+__device__ __forceinline__ void xstages(cpx<T>* S, cpx<T>* v, const cpx<T>* __restrict__ tw, int tid,
+                                        const ColIO<T>& io) {
+  constexpr int NS = ct_nstages(P);
+  if constexpr (s < NS) {
+    constexpr int R = REV ? ct_rad_rev(P, s) : ct_rad(P, s);
+    constexpr int Ns = REV ? ct_ns_rev(P, s) : ct_ns(P, s);
+    constexpr int SRC = s == 0 ? SRC0 : (int)XS_SMEM;
+    constexpr int DST = s == NS - 1 ? DSTL : (int)XS_SMEM;
+    xstage<T, P, W, P * W / 16, R, Ns, INV, SRC, DST>(S, v, tw, tid, io);
+    xstages<T, P, W, INV, REV, s + 1, SRC0, DSTL>(S, v, tw, tid, io);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ ColIO<T> col_io(const PassParams& p, int W, int n_in, int n_out, int dup) {
+  ColIO<T> io;
+  const long long obase_i = (long long)blockIdx.y * p.ai.os + (long long)blockIdx.z * p.ai.cs;
+  const long long obase_o = (long long)blockIdx.y * p.ao.os + (long long)blockIdx.z * p.ao.cs;
+  io.in = (const cpx<T>*)p.in + obase_i;
+  io.out = (cpx<T>*)p.out + obase_o;
+  io.ils = p.ai.ls;
+  io.ijs = p.ai.js;
+  io.ols = p.ao.ls;
+  io.ojs = p.ao.js;
+  io.q0 = blockIdx.x * W;
+  io.npen = p.npen;
+  io.n_in = n_in;
+  io.n_out = n_out;
+  io.dup = dup;
+  return io;
+}
+
+template <typename T, int PC, int WC>
+__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fwd_c2c_col(PassParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
+  cpx<T> v[16];
+  const ColIO<T> io = col_io<T>(p, WC, p.n_use, PC, -1);
+  xstages<T, PC, WC, false, false, 0, XS_GLOBAL, XS_GLOBAL>(S, v, (const cpx<T>*)p.tw, threadIdx.x, io);
+}
+
+template <typename T, int PC, int WC>
+__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_inv_c2c_col(PassParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
+  cpx<T> v[16];
+  const int dup = (p.type == T_PER && p.center == C_NODE && p.n_data > p.N) ? p.N : -1;
+  const ColIO<T> io = col_io<T>(p, WC, PC, p.n_data, dup);
+  xstages<T, PC, WC, true, false, 0, XS_GLOBAL, XS_GLOBAL>(S, v, (const cpx<T>*)p.tw, threadIdx.x, io);
+}
+
+template <typename T, int PC, int WC>
+__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fused_c2c_col(PassParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int P = PC, W = WC, NT = PC * WC / 16;
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
+  long long* goff = reinterpret_cast<long long*>(smraw + (size_t)P * (W + 1) * sizeof(cpx<T>));
+  T* k2p = reinterpret_cast<T*>(goff + W);
+  const int tid = threadIdx.x;
+  const int q0 = blockIdx.x * W;
+  for (int lane = tid; lane < W; lane += NT) pencil_green_base<T>(p, q0 + lane, blockIdx.y, &goff[lane], &k2p[lane]);
+  const int dup = (p.type == T_PER && p.center == C_NODE && p.n_data > p.N) ? p.N : -1;
+  const ColIO<T> io = col_io<T>(p, W, p.n_use, p.n_data, dup);
+  const cpx<T>* tw = (const cpx<T>*)p.tw;
+  cpx<T> v[16];
+  // forward: HBM -> ... -> registers (the first stage's barrier also publishes goff/k2p)
+  xstages<T, P, W, false, false, 0, XS_GLOBAL, XS_REGS>(S, v, tw, tid, io);
+  // u^ = G^ f^ on the 16 elements this thread holds: indices j + r P/RL
+  constexpr int RL = ct_rad(P, ct_nstages(P) - 1);
+  constexpr int NB = 16 / RL;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int idx = tid + b * NT;
+    const int lane = idx % W, j = idx / W;
+    const long long go = goff[lane];
+    const T kp = k2p[lane];
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const int k = j + r * (P / RL);
+      const T G = green_at<T>(p, go, kp, min(k, P - k));
+      v[b * RL + r] = cscale<T>(v[b * RL + r], G);
+    }
+  }
+  // inverse, radices in reverse order: registers -> ... -> HBM
+  xstages<T, P, W, true, true, 0, XS_REGS, XS_GLOBAL>(S, v, tw, tid, io);
+}
+
+// ---------------------------------------------------------------------------
+// Instantiation helpers: one launcher and one smem-limit setter per <T, PC, WC>.
+// ---------------------------------------------------------------------------
+template <typename T, int PC, int WC>
+cudaError_t launch_kind(int kind, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st) {
+  if constexpr (PC > 0) {
+    if (p.axis != 0) {  // column passes of complex data: register-chained kernels
+      switch (kind) {
+        case K_FWD_C2C: k_fwd_c2c_col<T, PC, WC><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
+        case K_INV_C2C: k_inv_c2c_col<T, PC, WC><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
+        case K_FUSED_C2C: k_fused_c2c_col<T, PC, WC><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
+        default: break;
+      }
+    }
+  }
+  switch (kind) {
+    case K_FWD_REAL: k_fwd_real<T, PC, WC><<<grid, nthr, smem, st>>>(p); break;
+    case K_INV_REAL: k_inv_real<T, PC, WC><<<grid, nthr, smem, st>>>(p); break;
+    case K_FWD_C2C: k_fwd_c2c<T, PC, WC><<<grid, nthr, smem, st>>>(p); break;
+    case K_INV_C2C: k_inv_c2c<T, PC, WC><<<grid, nthr, smem, st>>>(p); break;
+    case K_FUSED_REAL: k_fused_real<T, PC, WC><<<grid, nthr, smem, st>>>(p); break;
+    case K_FUSED_C2C: k_fused_c2c<T, PC, WC><<<grid, nthr, smem, st>>>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int PC, int WC>
+cudaError_t set_limits_kind() {
+  const int lim = 227 * 1024;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_fwd_real<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_inv_real<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_fwd_c2c<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_inv_c2c<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_fused_real<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if constexpr (PC > 0) {
+    if ((e = cudaFuncSetAttribute(k_fwd_c2c_col<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(k_inv_c2c_col<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(k_fused_c2c_col<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  }
+  return cudaFuncSetAttribute(k_fused_c2c<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
+}  // namespace flups

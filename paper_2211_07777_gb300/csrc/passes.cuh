@@ -59,6 +59,9 @@ struct PassParams {
   int type, center, N, n_data, P, n_modes;
   int ctypes;             // transform type of each vector component, 4 bits per component
   int n_use;              // data values used (node periodic: N)
+  int ndlog;              // log2 of a power of two >= n_data, n_use, n_modes (row-mode index loops)
+  int hlog;               // log2 of a power of two >= P/2 + 1
+  int ct;                 // 1: compile-time tile engine (P = 2^a, W from ct_tile_width)
   RadixPlan plan;
   const void* tw;         // exp(-2 pi i m/(2P)), m < 2P, path precision
   FusedGreen g;
@@ -73,5 +76,11 @@ cudaError_t launch_curl(int kind, int prec, const PassParams& p, dim3 grid, int 
 cudaError_t set_curl_smem_limits();
 cudaError_t launch_pass(int kind, int prec, const PassParams& p, dim3 grid, int nthreads, size_t smem, cudaStream_t st);
 cudaError_t set_pass_smem_limits();
+// compile-time tile engine: lanes per tile for P = 2^a (32 <= P <= 2048), 0 when not compiled
+int ct_tile_width(int P, int prec);
+cudaError_t launch_ct_f32(int P, int kind, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st);
+cudaError_t launch_ct_f64(int P, int kind, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st);
+cudaError_t set_limits_ct_f32();
+cudaError_t set_limits_ct_f64();
 
 }  // namespace flups
