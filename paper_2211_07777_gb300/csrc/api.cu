@@ -165,11 +165,27 @@ int make_twiddles(int P, int prec, void** out) {
   }
   const size_t bytes = (size_t)M * 2 * esize(prec);
   void* d = nullptr;
-  CK(cudaMalloc(&d, bytes));
+  if (prec != FLUPS_F64E) CK(cudaMalloc(&d, bytes));
   if (prec == FLUPS_F32) {
     std::vector<float> h(2 * M);
     for (int m = 0; m < M; ++m) { h[2 * m] = (float)re[m]; h[2 * m + 1] = (float)im[m]; }
     CK(cudaMemcpy(d, h.data(), bytes, cudaMemcpyHostToDevice));
+  } else if (prec == FLUPS_F64E) {
+    // double-float pairs (hi, lo) of the re and im parts, from the extended-precision values
+    std::vector<float> h(4 * M);
+    for (int m = 0; m < M; ++m) {
+      const long double a = 3.141592653589793238462643383279502884L * (long double)m / (long double)P;
+      const long double c = cosl(a), sn = -sinl(a);
+      const float ch = (float)c, sh = (float)sn;
+      h[4 * m] = ch;
+      h[4 * m + 1] = (float)(c - (long double)ch);
+      h[4 * m + 2] = sh;
+      h[4 * m + 3] = (float)(sn - (long double)sh);
+    }
+    CK(cudaMalloc(&d, (size_t)M * 16));
+    CK(cudaMemcpy(d, h.data(), (size_t)M * 16, cudaMemcpyHostToDevice));
+    *out = d;
+    return FLUPS_OK;
   } else {
     std::vector<double> h(2 * M);
     for (int m = 0; m < M; ++m) { h[2 * m] = re[m]; h[2 * m + 1] = im[m]; }
@@ -353,6 +369,26 @@ int setup_green(flups_solver_s* s, cudaStream_t st) {
       }
       s->ws_bytes += bytes;
     }
+    if (prec == FLUPS_F64E) {
+      // the double-float path reads a stored spectrum: evaluate the closed form in FP64 once
+      int gext[3];
+      long long n = 1;
+      for (int d = 0; d < 3; ++d) {
+        gext[d] = s->dir[d].gext;
+        n *= gext[d];
+      }
+      double* g64 = nullptr;
+      CK(cudaMalloc(&g64, n * sizeof(double)));
+      const double* tabs[3] = {(const double*)s->tabs[0], (const double*)s->tabs[1], (const double*)s->tabs[2]};
+      cudaError_t e = launch_green_spectral(g64, gext, tabs, s->green, 0.5 * s->eps * s->eps, 1.0 / Pprod, st);
+      if (!e) e = cudaMalloc(&s->green_dev, n * 8);
+      if (!e) e = launch_green_finalize(g64, s->green_dev, prec, n, 1.0, st);
+      cudaError_t e2 = cudaStreamSynchronize(st);
+      cudaFree(g64);
+      if (e || e2) return cuda_fail(e ? e : e2, "green spectral");
+      s->green_bytes = (double)n * 8;
+      s->ws_bytes += (size_t)n * 8;
+    }
     return FLUPS_OK;
   }
   // stored spectrum: sample G(k_s, r_u) in FP64, DCT-I along each unbounded-like direction
@@ -505,6 +541,7 @@ int build_passes(flups_solver_s* s) {
     L.p.out = s->W1;
     L.out_buf = 1;
     L.user_in = 1;
+    L.p.in_f64 = prec == FLUPS_F64E;
     L.bytes = arr_bytes(0) + arr_bytes(1);
     L.flops = ffts(L, true, 1);
     s->passes.push_back(L);
@@ -596,6 +633,7 @@ int build_passes(flups_solver_s* s) {
     L.p.in = s->W1;
     L.in_buf = 1;
     L.user_out = 1;
+    L.p.out_f64 = prec == FLUPS_F64E;
     L.bytes = arr_bytes(0) + arr_bytes(1);
     L.flops = ffts(L, true, 1);
     s->passes.push_back(L);
@@ -634,7 +672,7 @@ int flups_init_topo(const int n[3], int center, int ncomp, int prec, flups_topo*
   if (!n || !out) return FLUPS_EINVAL;
   if (center != FLUPS_CELL && center != FLUPS_NODE) return FLUPS_EINVAL;
   if (ncomp != 1 && ncomp != 3) return FLUPS_EINVAL;
-  if (prec != FLUPS_F32 && prec != FLUPS_F64) return FLUPS_EINVAL;
+  if (prec != FLUPS_F32 && prec != FLUPS_F64 && prec != FLUPS_F64E) return FLUPS_EINVAL;
   for (int d = 0; d < 3; ++d)
     if (n[d] < 2 || n[d] > 8193) return FLUPS_ESIZE;
   flups_topo_s* t = new (std::nothrow) flups_topo_s;
@@ -717,6 +755,12 @@ int flups_init_solver(flups_topo t, const int* bc, const double h[3], const doub
     }
   }
   if (rc == FLUPS_OK) rc = build_plan(s);
+  if (rc == FLUPS_OK && t->prec == FLUPS_F64E) {
+    // the double-float path is compiled for power-of-two transform lengths only, scalar operators
+    if (op == FLUPS_BIOT_SAVART) rc = FLUPS_EINVAL;
+    for (int d = 0; d < 3 && rc == FLUPS_OK; ++d)
+      if (ct_tile_width(s->dir[d].P, FLUPS_F64E) == 0) rc = FLUPS_ESIZE;
+  }
   if (rc == FLUPS_OK) {
     int du = 0;
     for (int d = 0; d < 3; ++d) du += s->dir[d].unb;

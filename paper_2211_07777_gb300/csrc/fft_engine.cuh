@@ -16,12 +16,30 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dfloat.cuh"
+
 namespace flups {
 
 template <typename T> struct cpx_t;
 template <> struct cpx_t<float> { using type = float2; };
 template <> struct cpx_t<double> { using type = double2; };
+template <> struct cpx_t<dfloat> { using type = cdfloat; };
 template <typename T> using cpx = typename cpx_t<T>::type;
+
+// read-only cached loads (the double-float types go through their vector twins)
+template <typename T> __device__ __forceinline__ cpx<T> ldg_c(const cpx<T>* p) { return __ldg(p); }
+template <> __device__ __forceinline__ cdfloat ldg_c<dfloat>(const cdfloat* p) {
+  const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+  cdfloat c;
+  c.x = dfloat(q.x, q.y);
+  c.y = dfloat(q.z, q.w);
+  return c;
+}
+template <typename T> __device__ __forceinline__ T ldg_r(const T* p) { return __ldg(p); }
+template <> __device__ __forceinline__ dfloat ldg_r<dfloat>(const dfloat* p) {
+  const float2 q = __ldg(reinterpret_cast<const float2*>(p));
+  return dfloat(q.x, q.y);
+}
 
 template <typename T> __device__ __forceinline__ cpx<T> mk(T re, T im) { cpx<T> c; c.x = re; c.y = im; return c; }
 template <typename T> __device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
@@ -162,7 +180,7 @@ __device__ __forceinline__ void stage(const cpx<T>* X, cpx<T>* Y, int LS, int P,
       const int step = tstride * k;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        const cpx<T> w = __ldg(&tw[r * step]);
+        const cpx<T> w = ldg_c<T>(&tw[r * step]);
         v[r] = INV ? cmulc<T>(v[r], w) : cmul<T>(v[r], w);
       }
     }
@@ -237,7 +255,7 @@ __device__ __forceinline__ void ct_stage(cpx<T>* S, const cpx<T>* __restrict__ t
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        const cpx<T> w = __ldg(&tw[r * k * tstep]);
+        const cpx<T> w = ldg_c<T>(&tw[r * k * tstep]);
         v[b][r] = INV ? cmulc<T>(v[b][r], w) : cmul<T>(v[b][r], w);
       }
     }

@@ -194,6 +194,46 @@ __global__ void k_green_finalize(const double* __restrict__ g, T* __restrict__ o
     out[i] = (T)(g[i] * scale);
 }
 
+// double-float storage: hi = nearest float, lo = nearest float of the remainder
+__global__ void k_green_finalize_df(const double* __restrict__ g, float2* __restrict__ out, long long n, double scale) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = g[i] * scale;
+    const float h = __double2float_rn(v);
+    out[i] = make_float2(h, __double2float_rn(v - (double)h));
+  }
+}
+
+// Fully spectral kernels evaluated in FP64 (stored spectrum of the double-float path):
+// tab[d][g] holds |w_d|^2, or the 7-point symbol for LGF2; G = scale * f(sum_d tab[d][g_d]).
+__global__ void k_green_spectral(double* __restrict__ g, int gx, int gy, int gz, const double* __restrict__ t0,
+                                 const double* __restrict__ t1, const double* __restrict__ t2, int kernel,
+                                 double eps2h, double scale) {
+  const long long tot = (long long)gx * gy * gz;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i0 = (int)(idx % gx);
+    const long long rest = idx / gx;
+    const int i1 = (int)(rest % gy), i2 = (int)(rest / gy);
+    const double k2 = t0[i0] + t1[i1] + t2[i2];
+    double v = 0.0;
+    if (k2 > 0.0) {
+      if (kernel == 0 || kernel == 100) {
+        v = -1.0 / k2;
+      } else {
+        const int m = kernel / 2;
+        const double s = k2 * eps2h;
+        double acc = 1.0, term = 1.0;
+        for (int j = 1; j < m; ++j) {
+          term = term * s / j;
+          acc += term;
+        }
+        v = -exp(-s) * acc / k2;
+      }
+    }
+    g[idx] = v * scale;
+  }
+}
+
 cudaError_t launch_green_sample(double* g, const GreenSampleParams& q, cudaStream_t st) {
   const long long tot = (long long)q.gext[0] * q.gext[1] * q.gext[2];
   long long blocks = (tot + 255) / 256;
@@ -206,7 +246,18 @@ cudaError_t launch_green_finalize(const double* g, void* out, int prec, long lon
   long long blocks = (n + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (prec == 0) k_green_finalize<float><<<(unsigned)blocks, 256, 0, st>>>(g, (float*)out, n, scale);
+  else if (prec == 2) k_green_finalize_df<<<(unsigned)blocks, 256, 0, st>>>(g, (float2*)out, n, scale);
   else k_green_finalize<double><<<(unsigned)blocks, 256, 0, st>>>(g, (double*)out, n, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_green_spectral(double* g, const int* gext, const double* const* tabs, int kernel, double eps2h,
+                                  double scale, cudaStream_t st) {
+  const long long n = (long long)gext[0] * gext[1] * gext[2];
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_green_spectral<<<(unsigned)blocks, 256, 0, st>>>(g, gext[0], gext[1], gext[2], tabs[0], tabs[1], tabs[2], kernel,
+                                                     eps2h, scale);
   return cudaGetLastError();
 }
 

@@ -22,6 +22,8 @@ struct GreenSampleParams {
 
 cudaError_t launch_green_sample(double* g, const GreenSampleParams& q, cudaStream_t st);
 cudaError_t launch_green_finalize(const double* g, void* out, int prec, long long n, double scale, cudaStream_t st);
+cudaError_t launch_green_spectral(double* g, const int* gext, const double* const* tabs, int kernel, double eps2h,
+                                  double scale, cudaStream_t st);
 cudaError_t launch_special_eval(int which, const double* x, const double* y, double* out, int n, double eps,
                                 const GreenSampleParams& q, cudaStream_t st);
 

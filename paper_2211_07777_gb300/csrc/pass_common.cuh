@@ -5,6 +5,20 @@
 
 namespace flups {
 
+// Real loads/stores of the pass arrays; on the double-float path the caller's
+// arrays are FP64 (same element size) and convert on the way in and out.
+template <typename T> __device__ __forceinline__ T ld_real(const T* a, long long off, int f64) { return a[off]; }
+template <> __device__ __forceinline__ dfloat ld_real<dfloat>(const dfloat* a, long long off, int f64) {
+  if (f64) return df_from_double(reinterpret_cast<const double*>(a)[off]);
+  const float2 q = reinterpret_cast<const float2*>(a)[off];
+  return dfloat(q.x, q.y);
+}
+template <typename T> __device__ __forceinline__ void st_real(T* a, long long off, T v, int f64) { a[off] = v; }
+template <> __device__ __forceinline__ void st_real<dfloat>(dfloat* a, long long off, dfloat v, int f64) {
+  if (f64) reinterpret_cast<double*>(a)[off] = df_to_double(v);
+  else reinterpret_cast<float2*>(a)[off] = make_float2(v.hi, v.lo);
+}
+
 // Transform type of component `comp` (4 bits per component).
 __device__ __forceinline__ int comp_type(const PassParams& p, int comp) { return (p.ctypes >> (4 * comp)) & 15; }
 
@@ -129,7 +143,7 @@ __device__ __forceinline__ void load_real_ext(const PassParams& p, int type, con
     else { c = idx & (W2 - 1); i = idx / W2; }
     const int q = q0 + c;
     T v = (T)0;
-    if (q < p.npen) v = in[(long long)q * p.ai.ls + (long long)i * p.ai.js];
+    if (q < p.npen) v = ld_real<T>(in, (long long)q * p.ai.ls + (long long)i * p.ai.js, p.in_f64);
     const int ii = rev ? nd - 1 - i : i;
     int pos[4], sg[4];
     const int n = images(t, p.center, N, ii, pos, sg);
@@ -161,14 +175,14 @@ __device__ __forceinline__ void store_real_data(const PassParams& p, int type, T
       const cpx<T> z = S[pos * LS + (c >> 1)];
       v = (c & 1) ? z.y : z.x;
     }
-    out[(long long)q * p.ao.ls + (long long)i * p.ao.js] = v;
+    st_real<T>(out, (long long)q * p.ao.ls + (long long)i * p.ao.js, v, p.out_f64);
   }
 }
 
 // Spectrum of pencil a (part 0) or b (part 1) at mode k from the packed FFT.
 template <typename T>
 __device__ __forceinline__ cpx<T> split(cpx<T> zk, cpx<T> zm, int part) {
-  const T h = (T)0.5;
+  const T h = T(0.5);
   return part == 0 ? mk<T>(h * (zk.x + zm.x), h * (zk.y - zm.y)) : mk<T>(h * (zk.y + zm.y), h * (zm.x - zk.x));
 }
 

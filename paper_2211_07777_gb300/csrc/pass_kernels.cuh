@@ -19,6 +19,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "pass_common.cuh"
 #include "passes.cuh"
 
@@ -75,7 +77,7 @@ __device__ __forceinline__ cpx<T> stored_mode(const PassParams& p, int type, con
   }
   const T c = ((const T*)in)[off_pencil + (long long)m * p.ai.js] * div;
   cpx<T> F = is_odd_origin(t) ? mk<T>((T)0, -c) : mk<T>(c, (T)0);
-  if (p.center == C_CELL) F = cmulc<T>(F, __ldg(&tw[kk]));
+  if (p.center == C_CELL) F = cmulc<T>(F, ldg_c<T>(&tw[kk]));
   return F;
 }
 
@@ -122,9 +124,9 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
       ((cpx<T>*)p.out)[obase_o + off] = X;
     } else {
       cpx<T> F = X;
-      if (cell) F = cmul<T>(X, __ldg(&tw[kk]));
+      if (cell) F = cmul<T>(X, ldg_c<T>(&tw[kk]));
       T v = oddo ? -F.y : F.x;
-      if (quarter) v *= (T)0.5;
+      if (quarter) v = v * T(0.5);
       ((T*)p.out)[obase_o + off] = v;
     }
   }
@@ -265,12 +267,15 @@ __device__ __forceinline__ void pencil_green_base(const PassParams& p, int q, in
 template <typename T>
 __device__ __forceinline__ T green_at(const PassParams& p, long long goff, T k2p, int g3) {
   const FusedGreen& g = p.g;
-  if (g.stored) {
-    const long long st3 = p.axis == 0 ? 1 : (p.axis == 1 ? (long long)g.gext[0] : (long long)g.gext[0] * g.gext[1]);
-    return __ldg(&((const T*)g.stored)[goff + g3 * st3]);
+  if constexpr (!std::is_same<T, dfloat>::value) {
+    if (!g.stored) {
+      const T k2 = k2p + ((const T*)g.tab[p.axis])[g3];
+      return green_closed<T>(g.kernel, k2, (T)g.eps2_half, (T)g.scale);
+    }
   }
-  const T k2 = k2p + ((const T*)g.tab[p.axis])[g3];
-  return green_closed<T>(g.kernel, k2, (T)g.eps2_half, (T)g.scale);
+  // stored spectrum (always, on the double-float path)
+  const long long st3 = p.axis == 0 ? 1 : (p.axis == 1 ? (long long)g.gext[0] : (long long)g.gext[0] * g.gext[1]);
+  return ldg_r<T>(&((const T*)g.stored)[goff + g3 * st3]);
 }
 
 template <typename T, int PC>
@@ -407,7 +412,7 @@ __device__ __forceinline__ void xstage(cpx<T>* S, cpx<T>* v, const cpx<T>* __res
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        const cpx<T> w = __ldg(&tw[r * k * tstep]);
+        const cpx<T> w = ldg_c<T>(&tw[r * k * tstep]);
         v[b * R + r] = INV ? cmulc<T>(v[b * R + r], w) : cmul<T>(v[b * R + r], w);
       }
     }

@@ -24,10 +24,12 @@ cudaError_t set_pass_smem_limits() {
   if (!e) e = set_limits_kind<double, 0, 0>();
   if (!e) e = set_limits_ct_f32();
   if (!e) e = set_limits_ct_f64();
+  if (!e) e = set_limits_ct_df();
   return e;
 }
 
 cudaError_t launch_pass(int kind, int prec, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st) {
+  if (prec == 2) return p.ct ? launch_ct_df(p.P, kind, p, grid, nthr, smem, st) : cudaErrorInvalidValue;
   if (p.ct) return prec == 0 ? launch_ct_f32(p.P, kind, p, grid, nthr, smem, st)
                              : launch_ct_f64(p.P, kind, p, grid, nthr, smem, st);
   return prec == 0 ? launch_kind<float, 0, 0>(kind, p, grid, nthr, smem, st)

@@ -62,6 +62,7 @@ struct PassParams {
   int ndlog;              // log2 of a power of two >= n_data, n_use, n_modes (row-mode index loops)
   int hlog;               // log2 of a power of two >= P/2 + 1
   int ct;                 // 1: compile-time tile engine (P = 2^a, W from ct_tile_width)
+  int in_f64, out_f64;    // double-float path: the input / output is the caller's FP64 array
   RadixPlan plan;
   const void* tw;         // exp(-2 pi i m/(2P)), m < 2P, path precision
   FusedGreen g;
@@ -82,5 +83,7 @@ cudaError_t launch_ct_f32(int P, int kind, const PassParams& p, dim3 grid, int n
 cudaError_t launch_ct_f64(int P, int kind, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st);
 cudaError_t set_limits_ct_f32();
 cudaError_t set_limits_ct_f64();
+cudaError_t launch_ct_df(int P, int kind, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st);
+cudaError_t set_limits_ct_df();
 
 }  // namespace flups

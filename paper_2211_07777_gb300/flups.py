@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libflups_gpu.so")
 
 EVEN, ODD, PER, UNB = 0, 1, 3, 4
 CELL, NODE = 0, 1
-F32, F64 = 0, 1
+F32, F64, F64E = 0, 1, 2
 POISSON, BIOT_SAVART = 0, 1
 SPECTRAL, HEJ0, HEJ2, HEJ4, HEJ6, HEJ8, HEJ10, LGF2 = 0, 1, 2, 4, 6, 8, 10, 100
 DIFF_SPECTRAL, DIFF_FD2, DIFF_FD4, DIFF_FD6 = 0, 2, 4, 6
