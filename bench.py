@@ -274,6 +274,7 @@ def run_ours(args):
 
     # parity check of this exact launch configuration against the oracle (rank 0, modest sizes only)
     err = None
+    ref = None
     if rank == 0 and pts <= 2 ** 22:
         solver.solve(phi, rhs, stream)
         torch.cuda.synchronize()
@@ -318,6 +319,20 @@ def run_ours(args):
         total_ms = float(t.item())
     ms_per_step = total_ms / K
     value = world * pts * K / (total_ms * 1e-3) / 1e6
+
+    # the same configuration in the other arithmetic paths (FP32 vs FP64 at the stated error)
+    variants = {}
+    if rank == 0 and not args.no_variants and args.workload.split("_")[1] in PRECS:
+        base = args.workload.rsplit("_", 1)[0]
+        for tag in ("f32", "f64", "f64e"):
+            name = f"{base}_{tag}"
+            if name == args.workload:
+                continue
+            try:
+                wv = workload(name)
+            except SystemExit:
+                continue
+            variants[tag] = measure_variant(F, torch, wv, f_host, ref, flush, stream, max(5, K // 2), args.warmup)
 
     # e2e: public API with pinned host buffers, H2D + solve + D2H every step
     h_in = torch.from_numpy(f_host.astype(np.float32 if prec == 0 else np.float64)).pin_memory()
@@ -366,6 +381,7 @@ def run_ours(args):
         "config": {"workload": wl["desc"], "name": args.workload, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "max_rel_err_vs_oracle": err,
+        "variants": variants,
         "passes": [{"kernel": KIND_NAMES[p["kind"]], "axis": p["axis"], "P": p["P"], "ms": float(m),
                     "gbs": p["bytes"] / (m * 1e-3) / 1e9} for p, m in zip(pinfo, mean_pass)],
         "solve_hbm_frac": solve_frac,
@@ -449,6 +465,36 @@ def run_served(args):
     return 0
 
 
+def measure_variant(F, torch, wl, f_host, ref, flush, stream, K, warmup):
+    """Time one other arithmetic path of the same workload (whole solves, CUDA events, L2 flushed)."""
+    dt = torch.float32 if wl["prec"] == 0 else torch.float64
+    s = F.Solver(wl["n"], wl["bc"], L=wl["L"], center=wl["center"], prec=wl["prec"], green=wl["kernel"],
+                 h=wl.get("h"))
+    try:
+        rhs = torch.from_numpy(f_host).to(stream.device, dt)
+        phi = torch.empty_like(rhs)
+        s.solve(phi, rhs, stream)
+        torch.cuda.synchronize()
+        err = None
+        if ref is not None:
+            err = float(np.abs(phi.double().cpu().numpy() - ref).max() / np.abs(ref).max())
+        for _ in range(warmup):
+            flush.zero_()
+            s.solve(phi, rhs, stream)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            s.solve(phi, rhs, stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    finally:
+        s.close()
+    return {"value": float(np.prod(wl["n"])) / (ms * 1e-3) / 1e6, "unit": "Mpts/s", "ms_per_step": ms,
+            "dtype": DTYPES[wl["prec"]], "max_rel_err_vs_oracle": err, "steps": K}
+
+
 def run_profile(args):
     import torch
 
@@ -476,6 +522,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="unb128_f64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip timing the other arithmetic paths")
     ap.add_argument("--served-requests", type=int, default=4096)
     ap.add_argument("--streams", type=int, default=8)
     ap.add_argument("--profile", action="store_true",
