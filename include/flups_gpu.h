@@ -113,9 +113,14 @@ int flups_solve(flups_solver s, void* phi, const void* rhs, void* stream);
  * memory gives full copy bandwidth; pageable memory works. */
 int flups_solve_host(flups_solver s, void* phi_host, const void* rhs_host, void* stream);
 
-/* Releases the plan, the Green spectrum, the twiddles and the workspace.  The
- * caller's arrays are never freed.  Safe on NULL. */
+/* Releases the plan, the Green spectrum and the workspace (twiddle tables
+ * are shared by all solvers of the process and kept until exit).  The
+ * caller's arrays are never freed.  Safe on NULL.  flups_cleanup frees
+ * synchronously; flups_cleanup_async frees in stream order on `stream`
+ * without synchronising the device, and requires that no work using the
+ * solver is still pending on other streams. */
 int flups_cleanup(flups_solver s);
+int flups_cleanup_async(flups_solver s, void* stream);
 
 /* Introspection (host-only, after flups_setup): number of kernel launches per
  * solve; transform order (3 direction indices); algorithmic bytes moved per

@@ -14,6 +14,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -155,7 +156,7 @@ namespace {
 size_t esize(int prec) { return prec == FLUPS_F32 ? 4 : 8; }
 
 // Twiddles exp(-2 pi i m/(2P)), m = 0..2P-1, in extended precision then rounded once.
-int make_twiddles(int P, int prec, void** out) {
+static int make_twiddles_uncached(int P, int prec, void** out) {
   const int M = 2 * P;
   std::vector<double> re(M), im(M);
   for (int m = 0; m < M; ++m) {
@@ -191,6 +192,30 @@ int make_twiddles(int P, int prec, void** out) {
     for (int m = 0; m < M; ++m) { h[2 * m] = re[m]; h[2 * m + 1] = im[m]; }
     CK(cudaMemcpy(d, h.data(), bytes, cudaMemcpyHostToDevice));
   }
+  *out = d;
+  return FLUPS_OK;
+}
+
+// Twiddle tables are shared by every plan of a process: one table per (device,
+// P, precision), created on first use and kept until exit (a few KB each), so
+// that plan setup and teardown allocate and free no twiddles.
+std::mutex g_tw_mu;
+std::map<long long, void*> g_tw_cache;
+
+int make_twiddles(int P, int prec, void** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  const long long key = ((long long)dev << 40) | ((long long)prec << 32) | (long long)P;
+  std::lock_guard<std::mutex> lk(g_tw_mu);
+  auto it = g_tw_cache.find(key);
+  if (it != g_tw_cache.end()) {
+    *out = it->second;
+    return FLUPS_OK;
+  }
+  void* d = nullptr;
+  const int rc = make_twiddles_uncached(P, prec, &d);
+  if (rc) return rc;
+  g_tw_cache[key] = d;
   *out = d;
   return FLUPS_OK;
 }
@@ -252,7 +277,7 @@ int swap_parity(int b) { return b == FLUPS_EVEN ? FLUPS_ODD : (b == FLUPS_ODD ? 
 // mode, or the finite-difference symbols (Section "Application: the
 // Biot-Savart solver"): order 2 sin(wh)/h, order 4 (4/3 sin wh - 1/6 sin 2wh)/h,
 // order 6 (3/2 sin wh - 3/10 sin 2wh + 1/30 sin 3wh)/h.
-int make_dsym(int P, double h, int diff, int prec, void** out) {
+int make_dsym(int P, double h, int diff, int prec, void** out, cudaStream_t st) {
   std::vector<double> v(P);
   for (int kk = 0; kk < P; ++kk) {
     const int sgn = (2 * kk <= P) ? kk : kk - P;
@@ -267,12 +292,14 @@ int make_dsym(int P, double h, int diff, int prec, void** out) {
     v[kk] = sym;
   }
   const size_t bytes = (size_t)P * esz(prec);
-  CK(cudaMalloc(out, bytes));
+  CK(cudaMallocAsync(out, bytes, st));
   if (prec == FLUPS_F32) {
     std::vector<float> f(v.begin(), v.end());
-    CK(cudaMemcpy(*out, f.data(), bytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(*out, f.data(), bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
   } else {
-    CK(cudaMemcpy(*out, v.data(), bytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(*out, v.data(), bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
   }
   return FLUPS_OK;
 }
@@ -360,12 +387,14 @@ int setup_green(flups_solver_s* s, cudaStream_t st) {
         }
       }
       const size_t bytes = dp.gext * esize(prec);
-      CK(cudaMalloc(&s->tabs[d], bytes));
+      CK(cudaMallocAsync(&s->tabs[d], bytes, st));
       if (prec == FLUPS_F32) {
         std::vector<float> f(tab.begin(), tab.end());
-        CK(cudaMemcpy(s->tabs[d], f.data(), bytes, cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(s->tabs[d], f.data(), bytes, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
       } else {
-        CK(cudaMemcpy(s->tabs[d], tab.data(), bytes, cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(s->tabs[d], tab.data(), bytes, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
       }
       s->ws_bytes += bytes;
     }
@@ -378,13 +407,13 @@ int setup_green(flups_solver_s* s, cudaStream_t st) {
         n *= gext[d];
       }
       double* g64 = nullptr;
-      CK(cudaMalloc(&g64, n * sizeof(double)));
+      CK(cudaMallocAsync(&g64, n * sizeof(double), st));
       const double* tabs[3] = {(const double*)s->tabs[0], (const double*)s->tabs[1], (const double*)s->tabs[2]};
       cudaError_t e = launch_green_spectral(g64, gext, tabs, s->green, 0.5 * s->eps * s->eps, 1.0 / Pprod, st);
-      if (!e) e = cudaMalloc(&s->green_dev, n * 8);
+      if (!e) e = cudaMallocAsync(&s->green_dev, n * 8, st);
       if (!e) e = launch_green_finalize(g64, s->green_dev, prec, n, 1.0, st);
+      cudaFreeAsync(g64, st);
       cudaError_t e2 = cudaStreamSynchronize(st);
-      cudaFree(g64);
       if (e || e2) return cuda_fail(e ? e : e2, "green spectral");
       s->green_bytes = (double)n * 8;
       s->ws_bytes += (size_t)n * 8;
@@ -409,9 +438,9 @@ int setup_green(flups_solver_s* s, cudaStream_t st) {
   q.hmax = std::fmax(s->h[0], std::fmax(s->h[1], s->h[2]));
   gauss_legendre(GL_N, q.gl_x, q.gl_w);
   double* g64 = nullptr;
-  CK(cudaMalloc(&g64, n * sizeof(double)));
+  CK(cudaMallocAsync(&g64, n * sizeof(double), st));
   cudaError_t e = launch_green_sample(g64, q, st);
-  if (e) { cudaFree(g64); return cuda_fail(e, "green sample"); }
+  if (e) { cudaFreeAsync(g64, st); return cuda_fail(e, "green sample"); }
   double vol = 1.0;
   for (int d = 0; d < 3; ++d) {
     const DirPlan& dp = s->dir[d];
@@ -426,24 +455,22 @@ int setup_green(flups_solver_s* s, cudaStream_t st) {
     gp.nm = dp.gext;
     gp.rp = radix_plan(gp.P);
     int rc = make_twiddles(gp.P, FLUPS_F64, &gp.tw);
-    if (rc) { cudaFree(g64); return rc; }
+    if (rc) { cudaFreeAsync(g64, st); return rc; }
     Launch L{};
     L.kind = K_FWD_REAL;
     fill_geom(L, gp, d, q.gext, q.gext, FLUPS_F64, true, FLUPS_NODE, 1);
     L.p.in = g64;
     L.p.out = g64;
     e = launch_pass(L.kind, FLUPS_F64, L.p, L.grid, L.nthr, L.smem, st);
-    cudaError_t e2 = cudaStreamSynchronize(st);
-    cudaFree(gp.tw);
-    if (e || e2) { cudaFree(g64); return cuda_fail(e ? e : e2, "green DCT-I"); }
+    if (e) { cudaFreeAsync(g64, st); return cuda_fail(e, "green DCT-I"); }
   }
   const double scale = vol / Pprod;
   const size_t bytes = n * esize(prec);
-  e = cudaMalloc(&s->green_dev, bytes);
-  if (e) { cudaFree(g64); return cuda_fail(e, "green alloc"); }
+  e = cudaMallocAsync(&s->green_dev, bytes, st);
+  if (e) { cudaFreeAsync(g64, st); return cuda_fail(e, "green alloc"); }
   e = launch_green_finalize(g64, s->green_dev, prec, n, scale, st);
+  cudaFreeAsync(g64, st);
   cudaError_t e2 = cudaStreamSynchronize(st);
-  cudaFree(g64);
   if (e || e2) return cuda_fail(e ? e : e2, "green finalize");
   s->green_bytes = (double)bytes;
   s->ws_bytes += bytes;
@@ -791,7 +818,7 @@ int flups_setup(flups_solver s, void* stream, size_t* workspace_bytes) {
   const size_t es = esize(prec);
   if (s->op == FLUPS_BIOT_SAVART) {
     for (int d = 0; d < 3; ++d) {
-      int rc = make_dsym(s->dir[d].P, s->dir[d].h, s->diff, prec, &s->dsym[d]);
+      int rc = make_dsym(s->dir[d].P, s->dir[d].h, s->diff, prec, &s->dsym[d], st);
       if (rc) return rc;
       s->ws_bytes += (size_t)s->dir[d].P * es;
     }
@@ -809,7 +836,7 @@ int flups_setup(flups_solver s, void* stream, size_t* workspace_bytes) {
   if (!s->shared) {
     for (int i = 1; i <= 2; ++i) {
       void** buf = i == 1 ? &s->W1 : &s->W2;
-      cudaError_t e = cudaMalloc(buf, wbytes[i]);
+      cudaError_t e = cudaMallocAsync(buf, wbytes[i], st);
       if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
         return FLUPS_ENOMEM;
@@ -958,17 +985,34 @@ int flups_solve_host(flups_solver s, void* phi_host, const void* rhs_host, void*
   return FLUPS_OK;
 }
 
+// Frees the solver's own device buffers on `st` (stream-ordered) or, with
+// st == nullptr, synchronously.  Twiddle tables are shared and stay.
+static void release(flups_solver s, cudaStream_t st, bool async) {
+  auto fr = [&](void* p) {
+    if (!p) return;
+    if (async) cudaFreeAsync(p, st);
+    else cudaFree(p);
+  };
+  for (int d = 0; d < 3; ++d) {
+    fr(s->tabs[d]);
+    fr(s->dsym[d]);
+  }
+  fr(s->W1);
+  fr(s->W2);
+  fr(s->green_dev);
+  fr(s->stage);
+}
+
 int flups_cleanup(flups_solver s) {
   if (!s) return FLUPS_OK;
-  for (int d = 0; d < 3; ++d) {
-    if (s->dir[d].tw) cudaFree(s->dir[d].tw);
-    if (s->tabs[d]) cudaFree(s->tabs[d]);
-    if (s->dsym[d]) cudaFree(s->dsym[d]);
-  }
-  if (s->W1) cudaFree(s->W1);
-  if (s->W2) cudaFree(s->W2);
-  if (s->green_dev) cudaFree(s->green_dev);
-  if (s->stage) cudaFree(s->stage);
+  release(s, nullptr, false);
+  delete s;
+  return FLUPS_OK;
+}
+
+int flups_cleanup_async(flups_solver s, void* stream) {
+  if (!s) return FLUPS_OK;
+  release(s, (cudaStream_t)stream, true);
   delete s;
   return FLUPS_OK;
 }

@@ -144,7 +144,9 @@ __device__ double hej2_du2(double k, double r, double eps, const GreenSamplePara
     lo = 0.0;
     hi = log(50.0 / a);
   }
-  const int npan = max(1, (int)ceil((hi - lo) / 0.25));
+  // exp(-a e^s - b e^-s) is bounded by 1 in the strip |Im s| < pi/2, so Gauss-Legendre
+  // panels of width 1 (Bernstein ellipse parameter ~6.4) converge like 6.4^-32 with 16 nodes
+  const int npan = max(1, (int)ceil(hi - lo));
   const double w = (hi - lo) / npan;
   double acc = 0.0;
   for (int pn = 0; pn < npan; ++pn) {

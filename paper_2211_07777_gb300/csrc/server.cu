@@ -8,12 +8,15 @@
 // problem key and shared by all slots of that key; a slot holds the device
 // input/output arrays and the workspace of one solve plus a CUDA graph of the
 // solve's kernel launches, captured once and replayed for every request the
-// slot serves.  Idle slots and plans are evicted least recently used first
-// when a new request needs the memory.  Completion times come from a host
-// function enqueued after the result's device-to-host copy.
+// slot serves.  New plans are set up by worker threads on their own streams
+// while the serving loop keeps admitting and completing other requests.
+// Idle slots and plans are evicted least recently used first when a new
+// request needs the memory.  Completion times come from a host function
+// enqueued after the result's device-to-host copy.
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <condition_variable>
 #include <chrono>
 #include <cstring>
 #include <deque>
@@ -51,6 +54,8 @@ struct Plan {
   std::vector<Slot*> slots;
   int inflight = 0;
   double last_use = 0;
+  std::atomic<int> state{0};  // 0 building, 1 ready, < 0 setup failed (status)
+  bool settled = false;       // transient setup memory returned to the budget
   size_t slot_bytes() const { return 2 * io + ws; }
 };
 
@@ -109,6 +114,13 @@ std::string key_of(const flups_request& r) {
 
 struct flups_server_s {
   size_t budget = 0, in_use = 0, peak = 0;
+  // plan setup workers
+  std::vector<std::thread> workers;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Plan*> builds;
+  bool stop = false;
+  int building = 0;
   std::vector<cudaStream_t> streams;
   cudaStream_t setup_stream = nullptr, capture_stream = nullptr;
   int next_stream = 0;
@@ -123,6 +135,26 @@ struct flups_server_s {
 namespace {
 
 int cu(cudaError_t e) { return e == cudaSuccess ? FLUPS_OK : (e == cudaErrorMemoryAllocation ? FLUPS_ENOMEM : FLUPS_ECUDA); }
+
+void worker_main(flups_server_s* sv, int device) {
+  cudaSetDevice(device);
+  cudaStream_t st = nullptr;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  for (;;) {
+    Plan* p = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      sv->cv.wait(lk, [&] { return sv->stop || !sv->builds.empty(); });
+      if (sv->builds.empty()) break;
+      p = sv->builds.front();
+      sv->builds.pop_front();
+    }
+    const int rc = flups_setup_shared(p->solver, st);
+    cudaStreamSynchronize(st);  // every allocation of this setup is complete before anyone frees it
+    p->state.store(rc == FLUPS_OK ? 1 : (rc < 0 ? rc : FLUPS_ECUDA), std::memory_order_release);
+  }
+  if (st) cudaStreamDestroy(st);
+}
 
 void free_slot(flups_server_s* sv, Plan* p, Slot* s) {
   if (s->graph) cudaGraphExecDestroy(s->graph);
@@ -143,7 +175,7 @@ void discard_plan(Plan* p) {
 void free_plan(flups_server_s* sv, Plan* p) {
   for (Slot* s : p->slots) free_slot(sv, p, s);
   p->slots.clear();
-  flups_cleanup(p->solver);
+  flups_cleanup_async(p->solver, sv->setup_stream);
   flups_topo_free(p->topo);
   sv->in_use -= p->resident;
   delete p;
@@ -178,7 +210,7 @@ bool make_room(flups_server_s* sv, size_t need, Plan* keep) {
     best = 1e300;
     for (auto& kv : sv->plans) {
       Plan* p = kv.second;
-      if (p != keep && p->inflight == 0 && p->slots.empty() && p->last_use < best) {
+      if (p != keep && p->inflight == 0 && p->slots.empty() && p->settled && p->last_use < best) {
         best = p->last_use;
         vp = p;
       }
@@ -216,13 +248,46 @@ int try_start(flups_server_s* sv, Pending& pd) {
   const std::string key = key_of(pd.rq);
   Plan* p = nullptr;
   auto it = sv->plans.find(key);
-  bool fresh = false;
-  if (it != sv->plans.end()) {
-    p = it->second;
-  } else {
+  if (it == sv->plans.end()) {
+    // a new plan: reserve its memory and hand its setup to a worker; the request waits queued
     int rc = new_plan(pd.rq, &p);
     if (rc) return rc;
-    fresh = true;
+    const size_t need = p->resident + p->transient + p->slot_bytes();
+    if (need > sv->budget) {
+      discard_plan(p);
+      return FLUPS_ENOMEM;
+    }
+    if (!make_room(sv, p->resident + p->transient, nullptr)) {
+      discard_plan(p);
+      return 0;
+    }
+    sv->in_use += p->resident + p->transient;
+    if (sv->in_use > sv->peak) sv->peak = sv->in_use;
+    p->last_use = now_s();
+    sv->plans[key] = p;
+    sv->st.plan_misses++;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->builds.push_back(p);
+      sv->building++;
+    }
+    sv->cv.notify_one();
+    return 0;
+  }
+  p = it->second;
+  const int state = p->state.load(std::memory_order_acquire);
+  if (state == 0) return 0;  // still building
+  if (!p->settled) {
+    sv->in_use -= p->transient;  // the setup's temporary memory is back
+    p->settled = true;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->building--;
+  }
+  if (state < 0) {
+    // setup failed: forget the plan (a later request may retry) and fail this one
+    sv->plans.erase(p->key);
+    free_plan(sv, p);
+    return state;
   }
   Slot* slot = nullptr;
   for (Slot* s : p->slots)
@@ -231,27 +296,8 @@ int try_start(flups_server_s* sv, Pending& pd) {
       break;
     }
   size_t need = slot ? 0 : p->slot_bytes();
-  if (fresh) need += p->resident + p->transient;
-  if (need > sv->budget) {
-    if (fresh) discard_plan(p);
-    return FLUPS_ENOMEM;
-  }
-  if (!make_room(sv, need, p)) {
-    if (fresh) discard_plan(p);
-    return 0;
-  }
-  if (fresh) {
-    int rc = flups_setup_shared(p->solver, sv->setup_stream);
-    if (rc) {
-      discard_plan(p);
-      return rc;
-    }
-    sv->plans[key] = p;
-    sv->in_use += p->resident;
-    sv->st.plan_misses++;
-  } else {
-    sv->st.plan_hits++;
-  }
+  if (need > sv->budget) return FLUPS_ENOMEM;
+  if (!make_room(sv, need, p)) return 0;
   if (!slot) {
     slot = new (std::nothrow) Slot;
     if (!slot) return FLUPS_ENOMEM;
@@ -336,8 +382,13 @@ void reap(flups_server_s* sv) {
     }
   }
   admit_queued(sv);
-  // nothing running and nothing admissible: the head request can never fit
-  if (sv->inflight.empty() && !sv->queue.empty()) {
+  // nothing running, nothing being set up and nothing admissible: the head request can never fit
+  int building;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    building = sv->building;
+  }
+  if (sv->inflight.empty() && !sv->queue.empty() && building == 0) {
     Pending pd = sv->queue.front();
     sv->queue.pop_front();
     sv->done.push_back({pd.ticket, -1.0, FLUPS_ENOMEM});
@@ -392,6 +443,9 @@ int flups_server_create(size_t hbm_budget, int nstreams, flups_server* out) {
     delete sv;
     return rc;
   }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (int i = 0; i < 3; ++i) sv->workers.emplace_back(worker_main, sv, dev);
   *out = sv;
   return FLUPS_OK;
 }
@@ -450,6 +504,7 @@ int flups_server_pending(flups_server sv, int* queued, int* running) {
 int flups_server_get_stats(flups_server sv, flups_server_stats* out) {
   if (!sv || !out) return FLUPS_EINVAL;
   *out = sv->st;
+  out->plan_hits = sv->st.admitted > sv->st.plan_misses ? sv->st.admitted - sv->st.plan_misses : 0;
   out->hbm_in_use = sv->in_use;
   out->hbm_peak = sv->peak;
   out->plans_cached = (long long)sv->plans.size();
@@ -458,6 +513,12 @@ int flups_server_get_stats(flups_server sv, flups_server_stats* out) {
 
 int flups_server_destroy(flups_server sv) {
   if (!sv) return FLUPS_OK;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+  }
+  sv->cv.notify_all();
+  for (std::thread& t : sv->workers) t.join();
   for (cudaStream_t s : sv->streams) cudaStreamSynchronize(s);
   reap(sv);
   for (InFlight* f : sv->inflight) delete f;

@@ -27,7 +27,7 @@ EXPORTED = (
     "flups_init_topo", "flups_topo_free", "flups_init_solver", "flups_setup", "flups_solve",
     "flups_solve_host", "flups_cleanup", "flups_solver_info", "flups_strerror", "flups_last_cuda_error",
     "flups_debug_special", "flups_solve_pass", "flups_pass_info", "flups_solve_periodic_noalloc",
-    "flups_setup_shared", "flups_workspace_size", "flups_solve_ws", "flups_solver_memory",
+    "flups_setup_shared", "flups_cleanup_async", "flups_workspace_size", "flups_solve_ws", "flups_solver_memory",
     "flups_server_create", "flups_server_submit", "flups_server_poll", "flups_server_wait", "flups_server_pending",
     "flups_server_get_stats", "flups_server_destroy",
 )
@@ -84,6 +84,7 @@ def lib():
         L.flups_solve_periodic_noalloc.argtypes = [vp, vp, ip, dp, vp]
         szp = ctypes.POINTER(ctypes.c_size_t)
         L.flups_setup_shared.argtypes = [vp, vp]
+        L.flups_cleanup_async.argtypes = [vp, vp]
         L.flups_workspace_size.argtypes = [vp, szp]
         L.flups_solve_ws.argtypes = [vp, vp, vp, vp, vp]
         L.flups_solver_memory.argtypes = [vp, szp, szp, szp]
