@@ -134,6 +134,10 @@ int flups_solver_info(flups_solver s, int* launches_per_solve, int order[3], dou
  * pass writes phi; the passes in between use the solver's workspace).  Lets a
  * caller time each kernel with events on its own stream. */
 int flups_solve_pass(flups_solver s, int i, void* phi, const void* rhs, void* stream);
+/* The whole solve with a CUDA event recorded before every pass and after the
+ * last one: events = launches_per_solve + 1 cudaEvent_t handles (passed as
+ * void*), owned by the caller.  For timing each kernel on its own stream. */
+int flups_solve_events(flups_solver s, void* phi, const void* rhs, void* stream, void* const* events);
 /* Pass i: kernel kind (0 forward real, 1 inverse real, 2 forward C2C,
  * 3 inverse C2C, 4 fused real, 5 fused C2C), transform axis, FFT length,
  * algorithmic bytes (arrays read and written once, Green spectrum read once)

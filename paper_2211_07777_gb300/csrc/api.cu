@@ -332,7 +332,10 @@ void fill_geom(Launch& L, const DirPlan& dp, int axis, const int* din, const int
   p.axis = axis;
   p.npen = axis == 0 ? din[1] * din[2] : din[0];
   int W, nthr;
-  const int wct = share == 1 ? ct_tile_width(dp.P, prec) : 0;  // the curl pass keeps the runtime engine
+  int wct = share == 1 ? ct_tile_width(dp.P, prec) : 0;  // the curl pass keeps the runtime engine
+  const int other = axis == 0 ? 1 : (axis == 1 ? din[2] : din[1]);
+  auto ctas = [&](int w) { return (long long)((p.npen + (packed ? 2 * w : w) - 1) / (packed ? 2 * w : w)) * other * ncomp; };
+  if (wct && prec != FLUPS_F64E && ctas(wct) < 2 * 152) wct = 0;  // small grid: narrower runtime tiles, more CTAs
   if (wct) {
     W = wct;
     nthr = dp.P * W / 16;
@@ -340,6 +343,12 @@ void fill_geom(Launch& L, const DirPlan& dp, int axis, const int* din, const int
     p.LS = W + 1;
   } else {
     tile_shape(dp.P, prec, p.npen, packed, &W, &nthr, share);
+    while (W > 1 && ctas(W) < 2 * 152) W /= 2;
+    {
+      int t = (dp.P * W + 15) / 16;
+      t = ((t + 31) / 32) * 32;
+      nthr = std::min(std::max(t, 64), prec == FLUPS_F32 ? 512 : 256);
+    }
     p.ct = 0;
     p.LS = (axis == 0 && W >= 8) ? W + 1 : W;
   }
@@ -948,6 +957,20 @@ int flups_solve_pass(flups_solver s, int i, void* phi, const void* rhs, void* st
                       ? launch_curl(L.kind, s->topo.prec, p, L.grid, L.nthr, L.smem, (cudaStream_t)stream)
                       : launch_pass(L.kind, s->topo.prec, p, L.grid, L.nthr, L.smem, (cudaStream_t)stream);
   if (e) return cuda_fail(e, "pass launch");
+  return FLUPS_OK;
+}
+
+int flups_solve_events(flups_solver s, void* phi, const void* rhs, void* stream, void* const* events) {
+  if (!s || !phi || !rhs || !events) return FLUPS_EINVAL;
+  if (!s->ready || s->shared) return FLUPS_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = (int)s->passes.size();
+  for (int i = 0; i < n; ++i) {
+    CK(cudaEventRecord((cudaEvent_t)events[i], st));
+    const int rc = flups_solve_pass(s, i, phi, rhs, stream);
+    if (rc) return rc;
+  }
+  CK(cudaEventRecord((cudaEvent_t)events[n], st));
   return FLUPS_OK;
 }
 

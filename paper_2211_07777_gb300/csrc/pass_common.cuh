@@ -137,18 +137,33 @@ __device__ __forceinline__ void load_real_ext(const PassParams& p, int type, con
   const bool rowmode = p.axis == 0;
   // row mode: index i fastest over a power-of-two stride (1 << ndlog) >= nd
   const int tot = rowmode ? (W2 << p.ndlog) : nd * W2;
-  for (int idx = tid; idx < tot; idx += nthr) {
-    int c, i;
-    if (rowmode) { i = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (i >= nd) continue; }
-    else { c = idx & (W2 - 1); i = idx / W2; }
-    const int q = q0 + c;
-    T v = (T)0;
-    if (q < p.npen) v = ld_real<T>(in, (long long)q * p.ai.ls + (long long)i * p.ai.js, p.in_f64);
-    const int ii = rev ? nd - 1 - i : i;
-    int pos[4], sg[4];
-    const int n = images(t, p.center, N, ii, pos, sg);
-    const int lane = c >> 1, part = c & 1;
-    for (int k = 0; k < n; ++k) Sr[2 * (pos[k] * LS + lane) + part] = sg[k] > 0 ? v : -v;
+  // batches of LOADB independent loads per thread before their values are used (latency hiding)
+  constexpr int LOADB = 8;
+  for (int base = tid; base < tot; base += LOADB * nthr) {
+    T v[LOADB];
+    int cc[LOADB], ii[LOADB];
+#pragma unroll
+    for (int u = 0; u < LOADB; ++u) {
+      const int idx = base + u * nthr;
+      int c = 0, i = -1;
+      if (idx < tot) {
+        if (rowmode) { i = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (i >= nd) i = -1; }
+        else { c = idx & (W2 - 1); i = idx / W2; }
+      }
+      cc[u] = c;
+      ii[u] = i;
+      const int q = q0 + c;
+      v[u] = (i >= 0 && q < p.npen) ? ld_real<T>(in, (long long)q * p.ai.ls + (long long)i * p.ai.js, p.in_f64) : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < LOADB; ++u) {
+      if (ii[u] < 0) continue;
+      const int dix = rev ? nd - 1 - ii[u] : ii[u];
+      int pos[4], sg[4];
+      const int n = images(t, p.center, N, dix, pos, sg);
+      const int lane = cc[u] >> 1, part = cc[u] & 1;
+      for (int k = 0; k < n; ++k) Sr[2 * (pos[k] * LS + lane) + part] = sg[k] > 0 ? v[u] : -v[u];
+    }
   }
 }
 
@@ -194,14 +209,26 @@ __device__ __forceinline__ void load_cplx(const PassParams& p, const cpx<T>* __r
   if (nu < p.P) zero_fill<T>(S, LS, W, nu, p.P, tid, nthr);
   const bool rowmode = p.axis == 0;
   const int tot = rowmode ? (W << p.ndlog) : nu * W;
-  for (int idx = tid; idx < tot; idx += nthr) {
-    int lane, i;
-    if (rowmode) { i = idx & ((1 << p.ndlog) - 1); lane = idx >> p.ndlog; if (i >= nu) continue; }
-    else { lane = idx & (W - 1); i = idx / W; }
-    const int q = q0 + lane;
-    cpx<T> v = mk<T>((T)0, (T)0);
-    if (q < p.npen) v = in[(long long)q * p.ai.ls + (long long)i * p.ai.js];
-    S[i * LS + lane] = v;
+  constexpr int LOADB = 8;
+  for (int base = tid; base < tot; base += LOADB * nthr) {
+    cpx<T> v[LOADB];
+    int ll[LOADB], ii[LOADB];
+#pragma unroll
+    for (int u = 0; u < LOADB; ++u) {
+      const int idx = base + u * nthr;
+      int lane = 0, i = -1;
+      if (idx < tot) {
+        if (rowmode) { i = idx & ((1 << p.ndlog) - 1); lane = idx >> p.ndlog; if (i >= nu) i = -1; }
+        else { lane = idx & (W - 1); i = idx / W; }
+      }
+      ll[u] = lane;
+      ii[u] = i;
+      const int q = q0 + lane;
+      v[u] = (i >= 0 && q < p.npen) ? in[(long long)q * p.ai.ls + (long long)i * p.ai.js] : mk<T>((T)0, (T)0);
+    }
+#pragma unroll
+    for (int u = 0; u < LOADB; ++u)
+      if (ii[u] >= 0) S[ii[u] * LS + ll[u]] = v[u];
   }
 }
 

@@ -148,16 +148,34 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   const bool rowmode = p.axis == 0;
   // row mode: k fastest over a power-of-two stride (1 << p.hlog) >= half + 1
   const int tot = rowmode ? (W << p.hlog) : (half + 1) * W;
-  for (int idx = tid; idx < tot; idx += nthr) {
-    int lane, k;
-    if (rowmode) { k = idx & ((1 << p.hlog) - 1); lane = idx >> p.hlog; if (k > half) continue; }
-    else { lane = idx & (W - 1); k = idx / W; }
-    const int qa = q0 + 2 * lane, qb = qa + 1;
-    cpx<T> Xa = mk<T>((T)0, (T)0), Xb = Xa;
-    if (qa < p.npen) Xa = stored_mode<T>(p, ctype, p.in, obase_i + (long long)qa * p.ai.ls, k, P, tw);
-    if (qb < p.npen) Xb = stored_mode<T>(p, ctype, p.in, obase_i + (long long)qb * p.ai.ls, k, P, tw);
-    S[k * LS + lane] = mk<T>(Xa.x - Xb.y, Xa.y + Xb.x);
-    if (k != 0 && 2 * k != P) S[(P - k) * LS + lane] = mk<T>(Xa.x + Xb.y, Xb.x - Xa.y);
+  constexpr int LOADB = 4;
+  for (int base = tid; base < tot; base += LOADB * nthr) {
+    cpx<T> Xa[LOADB], Xb[LOADB];
+    int ll[LOADB], kk[LOADB];
+#pragma unroll
+    for (int u = 0; u < LOADB; ++u) {
+      const int idx = base + u * nthr;
+      int lane = 0, k = -1;
+      if (idx < tot) {
+        if (rowmode) { k = idx & ((1 << p.hlog) - 1); lane = idx >> p.hlog; if (k > half) k = -1; }
+        else { lane = idx & (W - 1); k = idx / W; }
+      }
+      ll[u] = lane;
+      kk[u] = k;
+      const int qa = q0 + 2 * lane, qb = qa + 1;
+      Xa[u] = mk<T>((T)0, (T)0);
+      Xb[u] = Xa[u];
+      if (k >= 0 && qa < p.npen) Xa[u] = stored_mode<T>(p, ctype, p.in, obase_i + (long long)qa * p.ai.ls, k, P, tw);
+      if (k >= 0 && qb < p.npen) Xb[u] = stored_mode<T>(p, ctype, p.in, obase_i + (long long)qb * p.ai.ls, k, P, tw);
+    }
+#pragma unroll
+    for (int u = 0; u < LOADB; ++u) {
+      const int k = kk[u];
+      if (k < 0) continue;
+      const int lane = ll[u];
+      S[k * LS + lane] = mk<T>(Xa[u].x - Xb[u].y, Xa[u].y + Xb[u].x);
+      if (k != 0 && 2 * k != P) S[(P - k) * LS + lane] = mk<T>(Xa[u].x + Xb[u].y, Xb[u].x - Xa[u].y);
+    }
   }
   __syncthreads();
   S = run_fft<T, PC, WC, true>(p, S, second_buffer<T, PC>(p, S), tw, tid, nthr);

@@ -26,7 +26,7 @@ KERNELS = {"spectral": SPECTRAL, "hej0": HEJ0, "hej2": HEJ2, "hej4": HEJ4, "hej6
 EXPORTED = (
     "flups_init_topo", "flups_topo_free", "flups_init_solver", "flups_setup", "flups_solve",
     "flups_solve_host", "flups_cleanup", "flups_solver_info", "flups_strerror", "flups_last_cuda_error",
-    "flups_debug_special", "flups_solve_pass", "flups_pass_info", "flups_solve_periodic_noalloc",
+    "flups_debug_special", "flups_solve_pass", "flups_pass_info", "flups_solve_events", "flups_solve_periodic_noalloc",
     "flups_setup_shared", "flups_cleanup_async", "flups_workspace_size", "flups_solve_ws", "flups_solver_memory",
     "flups_server_create", "flups_server_submit", "flups_server_poll", "flups_server_wait", "flups_server_pending",
     "flups_server_get_stats", "flups_server_destroy",
@@ -81,6 +81,7 @@ def lib():
         L.flups_debug_special.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int, ctypes.c_double]
         L.flups_solve_pass.argtypes = [vp, ctypes.c_int, vp, vp, vp]
         L.flups_pass_info.argtypes = [vp, ctypes.c_int, ip, ip, ip, dp, dp]
+        L.flups_solve_events.argtypes = [vp, vp, vp, vp, ctypes.POINTER(vp)]
         L.flups_solve_periodic_noalloc.argtypes = [vp, vp, ip, dp, vp]
         szp = ctypes.POINTER(ctypes.c_size_t)
         L.flups_setup_shared.argtypes = [vp, vp]
@@ -194,6 +195,13 @@ def flups_solver_info(solver):
 
 def flups_solve_pass(solver, i, phi, rhs, stream=None):
     _check(lib().flups_solve_pass(solver, int(i), _ptr(phi), _ptr(rhs), _stream(stream)), "flups_solve_pass")
+
+
+def flups_solve_events(solver, phi, rhs, events, stream=None):
+    """events: sequence of launches+1 torch.cuda.Event (or raw handles)."""
+    hs = [e.cuda_event if hasattr(e, "cuda_event") else int(e) for e in events]
+    arr = (ctypes.c_void_p * len(hs))(*hs)
+    _check(lib().flups_solve_events(solver, _ptr(phi), _ptr(rhs), _stream(stream), arr), "flups_solve_events")
 
 
 def flups_pass_info(solver, i):
@@ -339,6 +347,9 @@ class Solver:
 
     def solve_pass(self, i, phi, rhs, stream=None):
         flups_solve_pass(self._s, i, phi, rhs, stream)
+
+    def solve_events(self, phi, rhs, events, stream=None):
+        flups_solve_events(self._s, phi, rhs, events, stream)
 
     def pass_info(self, i):
         return flups_pass_info(self._s, i)
