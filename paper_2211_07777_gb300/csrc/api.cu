@@ -362,6 +362,7 @@ void fill_geom(Launch& L, const DirPlan& dp, int axis, const int* din, const int
   p.P = dp.P;
   p.n_modes = dp.nm;
   p.n_use = (dp.type == T_PER) ? dp.N : dp.n_data;
+  p.hz = (p.ct && dp.type == T_UNB && center == FLUPS_CELL && 2 * dp.n_data == dp.P) ? 1 : 0;
   {
     int m = std::max(std::max(p.n_data, p.n_use), p.n_modes);
     p.ndlog = ilog2(m);

@@ -238,7 +238,11 @@ __host__ __device__ constexpr int ct_radix(int rem) {
   return rem == 32 ? 8 : (rem >= 16 ? 16 : rem);
 }
 
-template <typename T, int P, int W, int NT, int R, int Ns, bool INV>
+// ZIN: the stage's inputs with r >= R/2 are zero (first stage of a transform
+// whose second half is zero padding); ZOUT: its outputs with r >= R/2 are not
+// needed (last stage of a transform truncated to its first half).  Both are
+// compile-time, so the loads, stores and dead butterfly arithmetic vanish.
+template <typename T, int P, int W, int NT, int R, int Ns, bool INV, bool ZIN = false, bool ZOUT = false>
 __device__ __forceinline__ void ct_stage(cpx<T>* S, const cpx<T>* __restrict__ tw, int tid) {
   constexpr int LS = W + 1;
   constexpr int nbf = P / R;
@@ -251,7 +255,7 @@ __device__ __forceinline__ void ct_stage(cpx<T>* S, const cpx<T>* __restrict__ t
     const int idx = tid + b * NT;
     const int lane = idx % W, j = idx / W, k = j % Ns;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[b][r] = S[(j + r * nbf) * LS + lane];
+    for (int r = 0; r < R; ++r) v[b][r] = (ZIN && r >= R / 2) ? mk<T>((T)0, (T)0) : S[(j + r * nbf) * LS + lane];
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
@@ -268,17 +272,17 @@ __device__ __forceinline__ void ct_stage(cpx<T>* S, const cpx<T>* __restrict__ t
     const int lane = idx % W, j = idx / W, k = j % Ns;
     const int base = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) S[(base + r * Ns) * LS + lane] = v[b][r];
+    for (int r = 0; r < (ZOUT ? R / 2 : R); ++r) S[(base + r * Ns) * LS + lane] = v[b][r];
   }
   __syncthreads();
 }
 
-template <typename T, int P, int W, int NT, int Ns, bool INV>
+template <typename T, int P, int W, int NT, int Ns, bool INV, bool ZIN, bool ZOUT>
 __device__ __forceinline__ void ct_stages(cpx<T>* S, const cpx<T>* __restrict__ tw, int tid) {
   if constexpr (Ns < P) {
     constexpr int R = ct_radix(P / Ns);
-    ct_stage<T, P, W, NT, R, Ns, INV>(S, tw, tid);
-    ct_stages<T, P, W, NT, Ns * R, INV>(S, tw, tid);
+    ct_stage<T, P, W, NT, R, Ns, INV, ZIN && Ns == 1, ZOUT && Ns * R == P>(S, tw, tid);
+    ct_stages<T, P, W, NT, Ns * R, INV, ZIN, ZOUT>(S, tw, tid);
   }
 }
 
@@ -303,9 +307,9 @@ __host__ __device__ constexpr int ct_ns_rev(int P, int s) {
 }
 
 // In-place transform of the tile in S (lane stride W + 1); ends with a barrier.
-template <typename T, int P, int W, bool INV>
+template <typename T, int P, int W, bool INV, bool ZIN = false, bool ZOUT = false>
 __device__ __forceinline__ void fft_tile_ct(cpx<T>* S, const cpx<T>* __restrict__ tw, int tid) {
-  ct_stages<T, P, W, P * W / 16, 1, INV>(S, tw, tid);
+  ct_stages<T, P, W, P * W / 16, 1, INV, ZIN, ZOUT>(S, tw, tid);
 }
 
 }  // namespace flups

@@ -1,6 +1,7 @@
 // Device helpers shared by the pass kernels (passes.cu) and the Biot-Savart
 // fused kernels (curl.cu): extension geometry, tile loads and stores.
 #pragma once
+#include <type_traits>
 #include "passes.cuh"
 
 namespace flups {
@@ -123,22 +124,24 @@ __device__ __forceinline__ void zero_fill(cpx<T>* S, int LS, int W, int lo, int 
 }
 
 // Build the two-pencil extension of real data (pencils q0 + c, c < 2W).
+// skip_zero: the first FFT stage never reads the zero-padding rows (half-zero input)
 template <typename T, int WC = 0>
 __device__ __forceinline__ void load_real_ext(const PassParams& p, int type, const T* __restrict__ in, cpx<T>* S,
-                                              int q0, int tid, int nthr) {
+                                              int q0, int tid, int nthr, bool skip_zero = false) {
   const int W = WC ? WC : p.W, LS = WC ? WC + 1 : p.LS, N = p.N, nd = p.n_data;
   const int t = base_type(type);
   const bool rev = is_reversed(type);
   int lo[3], hi[3];
-  const int nz = zero_ranges(t, p.center, N, lo, hi);
+  const int nz = skip_zero ? 0 : zero_ranges(t, p.center, N, lo, hi);
   for (int r = 0; r < nz; ++r) zero_fill<T>(S, LS, W, lo[r], hi[r], tid, nthr);
   T* Sr = reinterpret_cast<T*>(S);
   const int W2 = 2 * W;
   const bool rowmode = p.axis == 0;
   // row mode: index i fastest over a power-of-two stride (1 << ndlog) >= nd
   const int tot = rowmode ? (W2 << p.ndlog) : nd * W2;
-  // batches of LOADB independent loads per thread before their values are used (latency hiding)
-  constexpr int LOADB = 8;
+  // batches of LOADB independent loads per thread before their values are used (latency
+  // hiding); the double-float path converts FP64 words on load and runs fastest unbatched
+  constexpr int LOADB = std::is_same<T, dfloat>::value ? 1 : 8;
   for (int base = tid; base < tot; base += LOADB * nthr) {
     T v[LOADB];
     int cc[LOADB], ii[LOADB];
@@ -204,9 +207,9 @@ __device__ __forceinline__ cpx<T> split(cpx<T> zk, cpx<T> zm, int part) {
 
 template <typename T, int WC = 0>
 __device__ __forceinline__ void load_cplx(const PassParams& p, const cpx<T>* __restrict__ in, cpx<T>* S, int q0,
-                                          int tid, int nthr) {
+                                          int tid, int nthr, bool skip_zero = false) {
   const int W = WC ? WC : p.W, LS = WC ? WC + 1 : p.LS, nu = p.n_use;
-  if (nu < p.P) zero_fill<T>(S, LS, W, nu, p.P, tid, nthr);
+  if (nu < p.P && !skip_zero) zero_fill<T>(S, LS, W, nu, p.P, tid, nthr);
   const bool rowmode = p.axis == 0;
   const int tot = rowmode ? (W << p.ndlog) : nu * W;
   constexpr int LOADB = 8;

@@ -42,11 +42,11 @@ struct Tile {
 };
 
 // FFT of the tile held in S (S2 = second buffer of the runtime engine); returns the buffer holding the result.
-template <typename T, int PC, int WC, bool INV>
+template <typename T, int PC, int WC, bool INV, bool ZIN = false, bool ZOUT = false>
 __device__ __forceinline__ cpx<T>* run_fft(const PassParams& p, cpx<T>* S, cpx<T>* S2, const cpx<T>* tw, int tid,
                                            int nthr) {
   if constexpr (PC > 0) {
-    fft_tile_ct<T, PC, WC, INV>(S, tw, tid);
+    fft_tile_ct<T, PC, WC, INV, ZIN, ZOUT>(S, tw, tid);
     return S;
   } else {
     return fft_tile<T, INV>(S, S2, p.LS, p.P, p.W, p.lw, p.plan, tw, tid, nthr);
@@ -85,7 +85,7 @@ __device__ __forceinline__ cpx<T> stored_mode(const PassParams& p, int type, con
 // Forward pass on real data: R2C (periodic, doubled unbounded) or r2r
 // coefficients (symmetric and semi-unbounded directions).
 // ---------------------------------------------------------------------------
-template <typename T, int PC, int WC>
+template <typename T, int PC, int WC, bool HZ>
 __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fwd_real(PassParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   using TL = Tile<T, PC, WC>;
@@ -96,10 +96,10 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   const long long obase_i = (long long)blockIdx.y * p.ai.os + (long long)blockIdx.z * p.ai.cs;
   const long long obase_o = (long long)blockIdx.y * p.ao.os + (long long)blockIdx.z * p.ao.cs;
   const int ctype = comp_type(p, blockIdx.z);
-  load_real_ext<T, WC>(p, ctype, (const T*)p.in + obase_i, S, q0, tid, nthr);
+  load_real_ext<T, WC>(p, ctype, (const T*)p.in + obase_i, S, q0, tid, nthr, HZ);
   __syncthreads();
   const cpx<T>* tw = (const cpx<T>*)p.tw;
-  S = run_fft<T, PC, WC, false>(p, S, second_buffer<T, PC>(p, S), tw, tid, nthr);
+  S = run_fft<T, PC, WC, false, HZ, false>(p, S, second_buffer<T, PC>(p, S), tw, tid, nthr);
 
   const int t = base_type(ctype);
   const bool cplx_out = (t == T_PER || t == T_UNB);
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   }
 }
 
-template <typename T, int PC, int WC>
+template <typename T, int PC, int WC, bool HZ>
 __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_inv_real(PassParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   using TL = Tile<T, PC, WC>;
@@ -178,14 +178,14 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     }
   }
   __syncthreads();
-  S = run_fft<T, PC, WC, true>(p, S, second_buffer<T, PC>(p, S), tw, tid, nthr);
+  S = run_fft<T, PC, WC, true, false, HZ>(p, S, second_buffer<T, PC>(p, S), tw, tid, nthr);
   store_real_data<T, WC>(p, ctype, (T*)p.out + obase_o, S, q0, tid, nthr);
 }
 
 // ---------------------------------------------------------------------------
 // Complex passes (second and third complex directions).
 // ---------------------------------------------------------------------------
-template <typename T, int PC, int WC>
+template <typename T, int PC, int WC, bool HZ>
 __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fwd_c2c(PassParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   using TL = Tile<T, PC, WC>;
@@ -195,9 +195,9 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   const int q0 = blockIdx.x * W;
   const long long obase_i = (long long)blockIdx.y * p.ai.os + (long long)blockIdx.z * p.ai.cs;
   const long long obase_o = (long long)blockIdx.y * p.ao.os + (long long)blockIdx.z * p.ao.cs;
-  load_cplx<T, WC>(p, (const cpx<T>*)p.in + obase_i, S, q0, tid, nthr);
+  load_cplx<T, WC>(p, (const cpx<T>*)p.in + obase_i, S, q0, tid, nthr, HZ);
   __syncthreads();
-  S = run_fft<T, PC, WC, false>(p, S, second_buffer<T, PC>(p, S), (const cpx<T>*)p.tw, tid, nthr);
+  S = run_fft<T, PC, WC, false, HZ, false>(p, S, second_buffer<T, PC>(p, S), (const cpx<T>*)p.tw, tid, nthr);
   cpx<T>* out = (cpx<T>*)p.out + obase_o;
   const bool rowmode = p.axis == 0;
   const int tot = P * W;
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   }
 }
 
-template <typename T, int PC, int WC>
+template <typename T, int PC, int WC, bool HZ>
 __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_inv_c2c(PassParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   using TL = Tile<T, PC, WC>;
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     S[k * LS + lane] = v;
   }
   __syncthreads();
-  S = run_fft<T, PC, WC, true>(p, S, second_buffer<T, PC>(p, S), (const cpx<T>*)p.tw, tid, nthr);
+  S = run_fft<T, PC, WC, true, false, HZ>(p, S, second_buffer<T, PC>(p, S), (const cpx<T>*)p.tw, tid, nthr);
   store_cplx_data<T, WC>(p, (cpx<T>*)p.out + obase_o, S, q0, tid, nthr);
 }
 
@@ -301,7 +301,7 @@ __device__ __forceinline__ size_t tile_bytes(const PassParams& p) {
   return (PC > 0 ? 1 : 2) * (size_t)p.P * p.LS * sizeof(cpx<T>);
 }
 
-template <typename T, int PC, int WC>
+template <typename T, int PC, int WC, bool HZ>
 __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fused_c2c(PassParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   using TL = Tile<T, PC, WC>;
@@ -314,10 +314,10 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   const int q0 = blockIdx.x * W;
   const long long obase = (long long)blockIdx.y * p.ai.os + (long long)blockIdx.z * p.ai.cs;
   for (int lane = tid; lane < W; lane += nthr) pencil_green_base<T>(p, q0 + lane, blockIdx.y, &goff[lane], &k2p[lane]);
-  load_cplx<T, WC>(p, (const cpx<T>*)p.in + obase, S, q0, tid, nthr);
+  load_cplx<T, WC>(p, (const cpx<T>*)p.in + obase, S, q0, tid, nthr, HZ);
   __syncthreads();
   const cpx<T>* tw = (const cpx<T>*)p.tw;
-  cpx<T>* X = run_fft<T, PC, WC, false>(p, S, S2, tw, tid, nthr);
+  cpx<T>* X = run_fft<T, PC, WC, false, HZ, false>(p, S, S2, tw, tid, nthr);
   const int tot = P * W;
   for (int idx = tid; idx < tot; idx += nthr) {
     const int lane = idx & (W - 1), k = idx / W;
@@ -326,11 +326,11 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     X[k * LS + lane] = cscale<T>(X[k * LS + lane], G);
   }
   __syncthreads();
-  X = run_fft<T, PC, WC, true>(p, X, X == S ? S2 : S, tw, tid, nthr);
+  X = run_fft<T, PC, WC, true, false, HZ>(p, X, X == S ? S2 : S, tw, tid, nthr);
   store_cplx_data<T, WC>(p, (cpx<T>*)p.out + obase, X, q0, tid, nthr);
 }
 
-template <typename T, int PC, int WC>
+template <typename T, int PC, int WC, bool HZ>
 __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fused_real(PassParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   using TL = Tile<T, PC, WC>;
@@ -344,10 +344,10 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   const long long obase = (long long)blockIdx.y * p.ai.os + (long long)blockIdx.z * p.ai.cs;
   for (int c = tid; c < 2 * W; c += nthr) pencil_green_base<T>(p, q0 + c, blockIdx.y, &goff[c], &k2p[c]);
   const int ctype = comp_type(p, blockIdx.z);
-  load_real_ext<T, WC>(p, ctype, (const T*)p.in + obase, S, q0, tid, nthr);
+  load_real_ext<T, WC>(p, ctype, (const T*)p.in + obase, S, q0, tid, nthr, HZ);
   __syncthreads();
   const cpx<T>* tw = (const cpx<T>*)p.tw;
-  cpx<T>* X = run_fft<T, PC, WC, false>(p, S, S2, tw, tid, nthr);
+  cpx<T>* X = run_fft<T, PC, WC, false, HZ, false>(p, S, S2, tw, tid, nthr);
   const bool quarter = is_quarter(base_type(ctype));
   const int half = P / 2;
   const int tot = (half + 1) * W;
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     if (k != 0 && 2 * k != P) X[km * LS + lane] = mk<T>(A.x + B.y, B.x - A.y);
   }
   __syncthreads();
-  X = run_fft<T, PC, WC, true>(p, X, X == S ? S2 : S, tw, tid, nthr);
+  X = run_fft<T, PC, WC, true, false, HZ>(p, X, X == S ? S2 : S, tw, tid, nthr);
   store_real_data<T, WC>(p, ctype, (T*)p.out + obase, X, q0, tid, nthr);
 }
 
@@ -396,7 +396,7 @@ struct ColIO {
   int dup;          // node-centred periodic: index 0 is also written to index dup (else -1)
 };
 
-template <typename T, int P, int W, int NT, int R, int Ns, bool INV, int SRC, int DST>
+template <typename T, int P, int W, int NT, int R, int Ns, bool INV, int SRC, int DST, bool ZIN, bool ZOUT>
 __device__ __forceinline__ void xstage(cpx<T>* S, cpx<T>* v, const cpx<T>* __restrict__ tw, int tid,
                                        const ColIO<T>& io) {
   constexpr int LS = W + 1;
@@ -412,7 +412,9 @@ __device__ __forceinline__ void xstage(cpx<T>* S, cpx<T>* v, const cpx<T>* __res
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int i = j + r * nbf;
-        if constexpr (SRC == XS_SMEM) {
+        if (ZIN && r >= R / 2) {
+          v[b * R + r] = mk<T>((T)0, (T)0);   // zero padding: inputs at i >= P/2
+        } else if constexpr (SRC == XS_SMEM) {
           v[b * R + r] = S[i * LS + lane];
         } else {
           const int q = io.q0 + lane;
@@ -443,7 +445,7 @@ __device__ __forceinline__ void xstage(cpx<T>* S, cpx<T>* v, const cpx<T>* __res
       const int lane = idx % W, j = idx / W, k = j % Ns;
       const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
+      for (int r = 0; r < (ZOUT ? R / 2 : R); ++r) {
         const int o = base + r * Ns;
         if constexpr (DST == XS_SMEM) {
           S[o * LS + lane] = v[b * R + r];
@@ -460,7 +462,7 @@ __device__ __forceinline__ void xstage(cpx<T>* S, cpx<T>* v, const cpx<T>* __res
   }
 }
 
-template <typename T, int P, int W, bool INV, bool REV, int s, int SRC0, int DSTL>
+template <typename T, int P, int W, bool INV, bool REV, int s, int SRC0, int DSTL, bool ZIN = false, bool ZOUT = false>
 __device__ __forceinline__ void xstages(cpx<T>* S, cpx<T>* v, const cpx<T>* __restrict__ tw, int tid,
                                         const ColIO<T>& io) {
   constexpr int NS = ct_nstages(P);
@@ -469,8 +471,8 @@ __device__ __forceinline__ void xstages(cpx<T>* S, cpx<T>* v, const cpx<T>* __re
     constexpr int Ns = REV ? ct_ns_rev(P, s) : ct_ns(P, s);
     constexpr int SRC = s == 0 ? SRC0 : (int)XS_SMEM;
     constexpr int DST = s == NS - 1 ? DSTL : (int)XS_SMEM;
-    xstage<T, P, W, P * W / 16, R, Ns, INV, SRC, DST>(S, v, tw, tid, io);
-    xstages<T, P, W, INV, REV, s + 1, SRC0, DSTL>(S, v, tw, tid, io);
+    xstage<T, P, W, P * W / 16, R, Ns, INV, SRC, DST, ZIN && s == 0, ZOUT && s == NS - 1>(S, v, tw, tid, io);
+    xstages<T, P, W, INV, REV, s + 1, SRC0, DSTL, ZIN, ZOUT>(S, v, tw, tid, io);
   }
 }
 
@@ -493,26 +495,26 @@ __device__ __forceinline__ ColIO<T> col_io(const PassParams& p, int W, int n_in,
   return io;
 }
 
-template <typename T, int PC, int WC>
+template <typename T, int PC, int WC, bool HZ>
 __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fwd_c2c_col(PassParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
   cpx<T> v[16];
   const ColIO<T> io = col_io<T>(p, WC, p.n_use, PC, -1);
-  xstages<T, PC, WC, false, false, 0, XS_GLOBAL, XS_GLOBAL>(S, v, (const cpx<T>*)p.tw, threadIdx.x, io);
+  xstages<T, PC, WC, false, false, 0, XS_GLOBAL, XS_GLOBAL, HZ, false>(S, v, (const cpx<T>*)p.tw, threadIdx.x, io);
 }
 
-template <typename T, int PC, int WC>
+template <typename T, int PC, int WC, bool HZ>
 __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_inv_c2c_col(PassParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
   cpx<T> v[16];
   const int dup = (p.type == T_PER && p.center == C_NODE && p.n_data > p.N) ? p.N : -1;
   const ColIO<T> io = col_io<T>(p, WC, PC, p.n_data, dup);
-  xstages<T, PC, WC, true, false, 0, XS_GLOBAL, XS_GLOBAL>(S, v, (const cpx<T>*)p.tw, threadIdx.x, io);
+  xstages<T, PC, WC, true, false, 0, XS_GLOBAL, XS_GLOBAL, false, HZ>(S, v, (const cpx<T>*)p.tw, threadIdx.x, io);
 }
 
-template <typename T, int PC, int WC>
+template <typename T, int PC, int WC, bool HZ>
 __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fused_c2c_col(PassParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int P = PC, W = WC, NT = PC * WC / 16;
@@ -527,7 +529,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   const cpx<T>* tw = (const cpx<T>*)p.tw;
   cpx<T> v[16];
   // forward: HBM -> ... -> registers (the first stage's barrier also publishes goff/k2p)
-  xstages<T, P, W, false, false, 0, XS_GLOBAL, XS_REGS>(S, v, tw, tid, io);
+  xstages<T, P, W, false, false, 0, XS_GLOBAL, XS_REGS, HZ, false>(S, v, tw, tid, io);
   // u^ = G^ f^ on the 16 elements this thread holds: indices j + r P/RL
   constexpr int RL = ct_rad(P, ct_nstages(P) - 1);
   constexpr int NB = 16 / RL;
@@ -545,51 +547,70 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     }
   }
   // inverse, radices in reverse order: registers -> ... -> HBM
-  xstages<T, P, W, true, true, 0, XS_REGS, XS_GLOBAL>(S, v, tw, tid, io);
+  xstages<T, P, W, true, true, 0, XS_REGS, XS_GLOBAL, false, HZ>(S, v, tw, tid, io);
 }
 
 // ---------------------------------------------------------------------------
 // Instantiation helpers: one launcher and one smem-limit setter per <T, PC, WC>.
 // ---------------------------------------------------------------------------
-template <typename T, int PC, int WC>
-cudaError_t launch_kind(int kind, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st) {
+template <typename T, int PC, int WC, bool HZ>
+cudaError_t launch_kind_hz(int kind, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st) {
   if constexpr (PC > 0) {
     if (p.axis != 0) {  // column passes of complex data: register-chained kernels
       switch (kind) {
-        case K_FWD_C2C: k_fwd_c2c_col<T, PC, WC><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
-        case K_INV_C2C: k_inv_c2c_col<T, PC, WC><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
-        case K_FUSED_C2C: k_fused_c2c_col<T, PC, WC><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
+        case K_FWD_C2C: k_fwd_c2c_col<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
+        case K_INV_C2C: k_inv_c2c_col<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
+        case K_FUSED_C2C: k_fused_c2c_col<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
         default: break;
       }
     }
   }
   switch (kind) {
-    case K_FWD_REAL: k_fwd_real<T, PC, WC><<<grid, nthr, smem, st>>>(p); break;
-    case K_INV_REAL: k_inv_real<T, PC, WC><<<grid, nthr, smem, st>>>(p); break;
-    case K_FWD_C2C: k_fwd_c2c<T, PC, WC><<<grid, nthr, smem, st>>>(p); break;
-    case K_INV_C2C: k_inv_c2c<T, PC, WC><<<grid, nthr, smem, st>>>(p); break;
-    case K_FUSED_REAL: k_fused_real<T, PC, WC><<<grid, nthr, smem, st>>>(p); break;
-    case K_FUSED_C2C: k_fused_c2c<T, PC, WC><<<grid, nthr, smem, st>>>(p); break;
+    case K_FWD_REAL: k_fwd_real<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); break;
+    case K_INV_REAL: k_inv_real<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); break;
+    case K_FWD_C2C: k_fwd_c2c<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); break;
+    case K_INV_C2C: k_inv_c2c<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); break;
+    case K_FUSED_REAL: k_fused_real<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); break;
+    case K_FUSED_C2C: k_fused_c2c<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
+// p.hz: the pass's transform is a cell-centred doubled (unbounded) one -- half of its
+// input is zero padding and half of its output is discarded (compile-time engine only)
 template <typename T, int PC, int WC>
-cudaError_t set_limits_kind() {
+cudaError_t launch_kind(int kind, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st) {
+  if constexpr (PC > 0) {
+    if (p.hz) return launch_kind_hz<T, PC, WC, true>(kind, p, grid, nthr, smem, st);
+  }
+  return launch_kind_hz<T, PC, WC, false>(kind, p, grid, nthr, smem, st);
+}
+
+template <typename T, int PC, int WC, bool HZ>
+cudaError_t set_limits_hz() {
   const int lim = 227 * 1024;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_fwd_real<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(k_inv_real<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(k_fwd_c2c<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(k_inv_c2c<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(k_fused_real<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_fwd_real<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_inv_real<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_fwd_c2c<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_inv_c2c<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(k_fused_real<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if constexpr (PC > 0) {
-    if ((e = cudaFuncSetAttribute(k_fwd_c2c_col<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(k_inv_c2c_col<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(k_fused_c2c_col<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(k_fwd_c2c_col<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(k_inv_c2c_col<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(k_fused_c2c_col<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   }
-  return cudaFuncSetAttribute(k_fused_c2c<T, PC, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  return cudaFuncSetAttribute(k_fused_c2c<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
+template <typename T, int PC, int WC>
+cudaError_t set_limits_kind() {
+  cudaError_t e = set_limits_hz<T, PC, WC, false>();
+  if constexpr (PC > 0) {
+    if (!e) e = set_limits_hz<T, PC, WC, true>();
+  }
+  return e;
 }
 
 }  // namespace flups

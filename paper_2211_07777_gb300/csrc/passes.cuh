@@ -63,6 +63,7 @@ struct PassParams {
   int hlog;               // log2 of a power of two >= P/2 + 1
   int ct;                 // 1: compile-time tile engine (P = 2^a, W from ct_tile_width)
   int in_f64, out_f64;    // double-float path: the input / output is the caller's FP64 array
+  int hz;                 // cell-centred doubled transform: half-zero input, half output kept (ct engine)
   RadixPlan plan;
   const void* tw;         // exp(-2 pi i m/(2P)), m < 2P, path precision
   FusedGreen g;
@@ -85,5 +86,8 @@ cudaError_t set_limits_ct_f32();
 cudaError_t set_limits_ct_f64();
 cudaError_t launch_ct_df(int P, int kind, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st);
 cudaError_t set_limits_ct_df();
+cudaError_t launch_ct_df_large(int P, int kind, const PassParams& p, dim3 grid, int nthr, size_t smem,
+                               cudaStream_t st);
+cudaError_t set_limits_ct_df_large();
 
 }  // namespace flups

@@ -1,5 +1,6 @@
 // Compile-time tile engine instantiations, double-float arithmetic (the FP64-class
-// emulated path; same tile widths as FP64, same bytes per element).
+// emulated path; same tile widths as FP64, same bytes per element).  P <= 256 here,
+// P >= 512 in passes_ct_df_large.cu (two translation units compile in parallel).
 #include <cuda_runtime.h>
 
 #include "pass_kernels.cuh"
@@ -12,11 +13,8 @@ cudaError_t launch_ct_df(int P, int kind, const PassParams& p, dim3 grid, int nt
     case 64: return launch_kind<dfloat, 64, 32>(kind, p, grid, nthr, smem, st);
     case 128: return launch_kind<dfloat, 128, 16>(kind, p, grid, nthr, smem, st);
     case 256: return launch_kind<dfloat, 256, 8>(kind, p, grid, nthr, smem, st);
-    case 512: return launch_kind<dfloat, 512, 8>(kind, p, grid, nthr, smem, st);
-    case 1024: return launch_kind<dfloat, 1024, 4>(kind, p, grid, nthr, smem, st);
-    case 2048: return launch_kind<dfloat, 2048, 2>(kind, p, grid, nthr, smem, st);
   }
-  return cudaErrorInvalidValue;
+  return launch_ct_df_large(P, kind, p, grid, nthr, smem, st);
 }
 
 cudaError_t set_limits_ct_df() {
@@ -25,9 +23,7 @@ cudaError_t set_limits_ct_df() {
   if (!e) e = set_limits_kind<dfloat, 64, 32>();
   if (!e) e = set_limits_kind<dfloat, 128, 16>();
   if (!e) e = set_limits_kind<dfloat, 256, 8>();
-  if (!e) e = set_limits_kind<dfloat, 512, 8>();
-  if (!e) e = set_limits_kind<dfloat, 1024, 4>();
-  if (!e) e = set_limits_kind<dfloat, 2048, 2>();
+  if (!e) e = set_limits_ct_df_large();
   return e;
 }
 
