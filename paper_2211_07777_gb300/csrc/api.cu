@@ -634,6 +634,17 @@ int build_passes(flups_solver_s* s) {
       g.gext[d] = s->dir[d].gext;
       g.fold[d] = (s->dir[d].role == R_C2C) ? s->dir[d].P : 0;
     }
+    if (!curl && !real && L.p.ct && o[2] != 0 && g.stored && dp.gext == dp.P / 2 + 1) {
+      // register-chained fused column kernel: stage the tile's Green slice in shared memory
+      // (cp.async at kernel start) when that keeps the kernel's CTAs per SM
+      const size_t gbytes = (size_t)L.p.W * (dp.P / 2 + 1) * esize(prec);
+      const int threads = L.nthr;
+      const int minb = std::max(1, (prec == FLUPS_F32 ? 1024 : 512) / threads);
+      if ((L.smem + gbytes + 1024) * minb <= 228 * 1024) {
+        L.smem += gbytes;
+        L.p.gpre = 1;
+      }
+    }
     g.kernel = s->green;
     g.eps2_half = 0.5 * s->eps * s->eps;
     g.scale = 1.0 / ((double)s->dir[0].P * s->dir[1].P * s->dir[2].P);

@@ -35,6 +35,17 @@ template <> __device__ __forceinline__ cdfloat ldg_c<dfloat>(const cdfloat* p) {
   c.y = dfloat(q.z, q.w);
   return c;
 }
+// Asynchronous global -> shared copy of one element (4 or 8 bytes, cp.async through L1),
+// completed by cp_async_wait_all() in the same thread (plus a barrier for other readers).
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* dst_smem, const void* src) {
+  static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async size");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <typename T> __device__ __forceinline__ T ldg_r(const T* p) { return __ldg(p); }
 template <> __device__ __forceinline__ dfloat ldg_r<dfloat>(const dfloat* p) {
   const float2 q = __ldg(reinterpret_cast<const float2*>(p));

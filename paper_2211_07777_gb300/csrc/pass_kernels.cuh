@@ -521,9 +521,27 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
   long long* goff = reinterpret_cast<long long*>(smraw + (size_t)P * (W + 1) * sizeof(cpx<T>));
   T* k2p = reinterpret_cast<T*>(goff + W);
+  // stored spectrum slice of this tile, W lanes x (P/2 + 1) folded modes (p.gpre)
+  T* Gs = reinterpret_cast<T*>(smraw + (size_t)P * (W + 1) * sizeof(cpx<T>) + (size_t)W * (sizeof(long long) + sizeof(T)));
+  constexpr int GH = P / 2 + 1;
   const int tid = threadIdx.x;
   const int q0 = blockIdx.x * W;
-  for (int lane = tid; lane < W; lane += NT) pencil_green_base<T>(p, q0 + lane, blockIdx.y, &goff[lane], &k2p[lane]);
+  if (p.gpre) {
+    // asynchronous copy (cp.async) of the Green slice, overlapped with the forward transform;
+    // NT is a multiple of W, so each thread serves one lane
+    const int lane = tid % W;
+    long long go;
+    T kp;
+    pencil_green_base<T>(p, q0 + lane, blockIdx.y, &go, &kp);
+    if (q0 + lane < p.npen) {
+      const long long st3 = p.axis == 1 ? (long long)p.g.gext[0] : (long long)p.g.gext[0] * p.g.gext[1];
+      const T* src = (const T*)p.g.stored + go;
+      for (int g3 = tid / W; g3 < GH; g3 += NT / W) cp_async_elem<sizeof(T)>(&Gs[g3 * W + lane], src + g3 * st3);
+    }
+    cp_async_commit();
+  } else {
+    for (int lane = tid; lane < W; lane += NT) pencil_green_base<T>(p, q0 + lane, blockIdx.y, &goff[lane], &k2p[lane]);
+  }
   const int dup = (p.type == T_PER && p.center == C_NODE && p.n_data > p.N) ? p.N : -1;
   const ColIO<T> io = col_io<T>(p, W, p.n_use, p.n_data, dup);
   const cpx<T>* tw = (const cpx<T>*)p.tw;
@@ -533,17 +551,32 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   // u^ = G^ f^ on the 16 elements this thread holds: indices j + r P/RL
   constexpr int RL = ct_rad(P, ct_nstages(P) - 1);
   constexpr int NB = 16 / RL;
+  if (p.gpre) {
+    cp_async_wait_all();
+    __syncthreads();
 #pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    const int idx = tid + b * NT;
-    const int lane = idx % W, j = idx / W;
-    const long long go = goff[lane];
-    const T kp = k2p[lane];
+    for (int b = 0; b < NB; ++b) {
+      const int idx = tid + b * NT;
+      const int lane = idx % W, j = idx / W;
 #pragma unroll
-    for (int r = 0; r < RL; ++r) {
-      const int k = j + r * (P / RL);
-      const T G = green_at<T>(p, go, kp, min(k, P - k));
-      v[b * RL + r] = cscale<T>(v[b * RL + r], G);
+      for (int r = 0; r < RL; ++r) {
+        const int k = j + r * (P / RL);
+        v[b * RL + r] = cscale<T>(v[b * RL + r], Gs[min(k, P - k) * W + lane]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int idx = tid + b * NT;
+      const int lane = idx % W, j = idx / W;
+      const long long go = goff[lane];
+      const T kp = k2p[lane];
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const int k = j + r * (P / RL);
+        const T G = green_at<T>(p, go, kp, min(k, P - k));
+        v[b * RL + r] = cscale<T>(v[b * RL + r], G);
+      }
     }
   }
   // inverse, radices in reverse order: registers -> ... -> HBM

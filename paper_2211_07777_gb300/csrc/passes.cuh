@@ -64,6 +64,7 @@ struct PassParams {
   int ct;                 // 1: compile-time tile engine (P = 2^a, W from ct_tile_width)
   int in_f64, out_f64;    // double-float path: the input / output is the caller's FP64 array
   int hz;                 // cell-centred doubled transform: half-zero input, half output kept (ct engine)
+  int gpre;               // fused column pass: copy the tile's stored Green slice to shared memory up front
   RadixPlan plan;
   const void* tw;         // exp(-2 pi i m/(2P)), m < 2P, path precision
   FusedGreen g;
