@@ -396,26 +396,72 @@ struct ColIO {
   int dup;          // node-centred periodic: index 0 is also written to index dup (else -1)
 };
 
+// Shared-memory row layout of the column kernels.  A wavefront of shared
+// memory serves 128 bytes; when a tile row (W elements) is narrower, G = 128 /
+// (W sizeof(cpx<T>)) rows share a wavefront, and the row strides of the stages
+// (1 for every load and for stores with Ns > 1, R for the Ns = 1 stores) would
+// land them on the same banks.  Rows are then permuted within aligned groups of
+// G: row i is kept in slot i ^ f(i >> lg G), f = XOR of the (lg G)-bit chunks of
+// its argument.  f is linear over disjoint bit fields, and G aligned rows
+// i0 + t d (d a power of two) differ in one (lg G)-bit field, so they land in G
+// distinct slots.  Wide rows (G = 1) keep the padded stride W + 1.
+template <typename T, int W>
+struct ColRows {
+  static constexpr int EB = (int)sizeof(cpx<T>);
+  static constexpr int G = (W * EB >= 128) ? 1 : 128 / (W * EB);
+  static_assert(G == 1 || G == 2 || G == 4, "row groups of 1, 2 or 4");
+  static constexpr int LG = G == 4 ? 2 : (G == 2 ? 1 : 0);
+  static constexpr int LS = G == 1 ? W + 1 : W;
+  __host__ __device__ static constexpr int fold_c(int x) {
+    int f = 0;
+    if (G > 1)
+      for (; x > 0; x >>= LG) f ^= x & (G - 1);
+    return f;
+  }
+  __device__ __forceinline__ static int fold(int x) {
+    if constexpr (G == 2) {
+      return __popc(x) & 1;
+    } else if constexpr (G == 4) {
+      x ^= x >> 16;
+      x ^= x >> 8;
+      x ^= x >> 4;
+      x ^= x >> 2;
+      return x & 3;
+    } else {
+      return 0;
+    }
+  }
+};
+
 template <typename T, int P, int W, int NT, int R, int Ns, bool INV, int SRC, int DST, bool ZIN, bool ZOUT>
 __device__ __forceinline__ void xstage(cpx<T>* S, cpx<T>* v, const cpx<T>* __restrict__ tw, int tid,
                                        const ColIO<T>& io) {
-  constexpr int LS = W + 1;
+  using CR = ColRows<T, W>;
+  constexpr int LS = CR::LS, LG = CR::LG;
   constexpr int nbf = P / R;
   constexpr int NB = (nbf * W) / NT;
   static_assert(NB * R == 16, "16 elements per thread");
+  static_assert(CR::G == 1 || (nbf >= CR::G && R >= CR::G && (Ns == 1 || Ns >= CR::G)), "row permutation fields");
   constexpr int tstep = (2 * P) / (Ns * R);
   if constexpr (SRC != XS_REGS) {
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int idx = tid + b * NT;
       const int lane = idx % W, j = idx / W;
+      // load rows j + r nbf (j < nbf): the permutation acts on j's field and r's field separately
+      const int jx = j ^ CR::fold(j >> LG);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int i = j + r * nbf;
         if (ZIN && r >= R / 2) {
           v[b * R + r] = mk<T>((T)0, (T)0);   // zero padding: inputs at i >= P/2
         } else if constexpr (SRC == XS_SMEM) {
-          v[b * R + r] = S[i * LS + lane];
+          if constexpr (CR::G == 1) {
+            v[b * R + r] = S[i * LS + lane];
+          } else {
+            const int hi = r * nbf;
+            v[b * R + r] = S[((jx ^ CR::fold_c(hi >> LG)) + hi) * W + lane];
+          }
         } else {
           const int q = io.q0 + lane;
           v[b * R + r] = (q < io.npen && i < io.n_in) ? io.in[(long long)q * io.ils + (long long)i * io.ijs]
@@ -444,11 +490,21 @@ __device__ __forceinline__ void xstage(cpx<T>* S, cpx<T>* v, const cpx<T>* __res
       const int idx = tid + b * NT;
       const int lane = idx % W, j = idx / W, k = j % Ns;
       const int base = (j - k) * R + k;
+      // store rows base + r Ns: fields k | r Ns | (j - k) R are disjoint; for Ns = 1 the low
+      // (lg G) bits come from r, otherwise from k
+      const int bx = (Ns == 1) ? CR::fold(base >> LG) : (base ^ CR::fold(base >> LG));
 #pragma unroll
       for (int r = 0; r < (ZOUT ? R / 2 : R); ++r) {
         const int o = base + r * Ns;
         if constexpr (DST == XS_SMEM) {
-          S[o * LS + lane] = v[b * R + r];
+          if constexpr (CR::G == 1) {
+            S[o * LS + lane] = v[b * R + r];
+          } else if constexpr (Ns == 1) {
+            S[(base + (r ^ CR::fold_c(r >> LG) ^ bx)) * W + lane] = v[b * R + r];
+          } else {
+            const int hi = r * Ns;
+            S[((bx ^ CR::fold_c(hi >> LG)) + hi) * W + lane] = v[b * R + r];
+          }
         } else {
           const int q = io.q0 + lane;
           if (q < io.npen) {
