@@ -20,6 +20,17 @@ convergence tables and against independent quadrature:
       G(k_s, r) = - int_{eps^2/2}^inf exp(-t |k_s|^2) (4 pi t)^(-d_u/2) exp(-r^2/(4t)) dt
 
   with the closed forms below for d_u = 3, for d_u = 1 and for k_s = 0.
+* HEJ2m, m >= 2, with d_u unbounded directions: the spectral kernel
+  -Gamma(m, s)/((m-1)! |k|^2), s = |k|^2 eps^2/2, equals
+  -int_a^inf t^{m-1} |k|^{2(m-1)} e^{-t|k|^2} dt/(m-1)!  (a = eps^2/2), and
+  |k|^{2n} e^{-t|k|^2} = (-d/dt)^n e^{-t|k|^2}.  The partial inverse transform
+  over the unbounded directions turns e^{-t|k|^2} into the heat kernel
+  h(t) = exp(-t |k_s|^2) (4 pi t)^(-d_u/2) exp(-r^2/(4t)); integrating by parts
+  m - 1 times leaves the HEJ2 kernel plus boundary terms at t = a:
+
+      G_2m(k_s, r) = G_2(k_s, r) + sum_{j=1}^{m-1} (-1)^j a^j h^(j-1)(a) / j!
+
+  (the terms at t = inf vanish for k_s > 0 or d_u = 3).
 * HEJ0 (fully unbounded, spectral truncation of the kernel at |k| = pi/h):
   G = -Si(pi r / h)/(2 pi^2 r),  G(0) = -1/(2 pi h).
 """
@@ -173,3 +184,58 @@ def hej2_mixed(du: int, kmag: np.ndarray, r: np.ndarray, eps: float) -> np.ndarr
     if du == 1:
         return hej2_1d(kmag, r, eps)
     raise ValueError("du must be 1, 2 or 3 here")
+
+
+# ---------------------------------------------------------------------------
+# Higher-order regularised kernels (HEJ4 ... HEJ10) with unbounded directions.
+# ---------------------------------------------------------------------------
+def heat_kernel_derivatives(n: int, t: float, q: np.ndarray, du: int, b: np.ndarray):
+    """[h^(0)(t), ..., h^(n)(t)] for h(t) = e^{-t q} (4 pi t)^(-du/2) e^{-b/t},
+    by the general Leibniz rule over the three factors:
+      (e^{-tq})^(i)        = (-q)^i e^{-tq}
+      (t^{-du/2})^(i)      = prod_{l<i} (-du/2 - l) t^{-du/2-i}
+      (e^{-b/t})^(i)       = e^{-b/t} P_i(1/t),  P_0 = 1,  P_{i+1} = P_i' + (b/t^2) P_i
+    (P_i is kept as coefficients of powers of u = 1/t:  d/dt u^p = -p u^{p+1})."""
+    q = np.asarray(q, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    u = 1.0 / t
+    A = [(-q) ** i * np.exp(-t * q) for i in range(n + 1)]
+    B = []
+    for i in range(n + 1):
+        c = 1.0
+        for l in range(i):
+            c *= -du / 2.0 - l
+        B.append(c * (4.0 * math.pi) ** (-du / 2.0) * t ** (-du / 2.0 - i))
+    polys = [{0: np.ones_like(b)}]
+    for i in range(n):
+        nxt = {}
+        for pw, c in polys[-1].items():
+            if pw > 0:
+                nxt[pw + 1] = nxt.get(pw + 1, 0.0) - pw * c
+            nxt[pw + 2] = nxt.get(pw + 2, 0.0) + b * c
+        polys.append(nxt)
+    eb = np.exp(-b * u)
+    C = [eb * sum(c * u ** pw for pw, c in P.items()) for P in polys]
+    out = []
+    for m in range(n + 1):
+        acc = 0.0
+        for i in range(m + 1):
+            for j in range(m - i + 1):
+                l = m - i - j
+                coef = math.factorial(m) // (math.factorial(i) * math.factorial(j) * math.factorial(l))
+                acc = acc + coef * A[i] * B[j] * C[l]
+        out.append(acc)
+    return out
+
+
+def hej_mixed(m: int, du: int, kmag: np.ndarray, r: np.ndarray, eps: float) -> np.ndarray:
+    """HEJ2m kernel (order 2m) with du unbounded directions, |k_s| = kmag, distance r."""
+    kmag, r = np.broadcast_arrays(np.asarray(kmag, dtype=np.float64), np.asarray(r, dtype=np.float64))
+    g = hej2_mixed(du, kmag, r, eps)
+    if m == 1:
+        return g
+    a = eps * eps / 2.0
+    hd = heat_kernel_derivatives(m - 2, a, kmag * kmag, du, r * r / 4.0)
+    for j in range(1, m):
+        g = g + (-1.0) ** j * a ** j * hd[j - 1] / math.factorial(j)
+    return g

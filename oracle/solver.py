@@ -239,8 +239,8 @@ def green_spectrum(prob: Problem, shape_ext) -> np.ndarray:
     k2, r2 = np.broadcast_arrays(k2, r2)
     kmag = np.sqrt(k2)
     r = np.sqrt(r2)
-    if prob.kernel == "hej2":
-        g = _green.hej2_mixed(du, kmag, r, prob.eps)
+    if prob.kernel in ("hej2", "hej4", "hej6", "hej8", "hej10"):
+        g = _green.hej_mixed(int(prob.kernel[3:]) // 2, du, kmag, r, prob.eps)
     elif prob.kernel == "hej0" and du == 3:
         g = _green.hej0_3d(r, max(prob.h))
     else:

@@ -173,7 +173,8 @@ def test_printed_symmetric_periodic(kernel, npts):
     _check_printed(err, _G["symmetric_periodic"][kernel][npts])
 
 
-@pytest.mark.parametrize("kernel,npts", [("hej2", "33"), ("hej2", "65"), ("hej0", "33"), ("hej0", "65")])
+@pytest.mark.parametrize("npts", ["33", "65"])
+@pytest.mark.parametrize("kernel", ["hej2", "hej4", "hej6", "hej8", "hej10", "hej0"])
 def test_printed_unbounded(kernel, npts):
     N = int(npts) - 1
     phi, f = analytic.case_unbounded(N)
@@ -184,13 +185,14 @@ def test_printed_unbounded(kernel, npts):
 
 
 @pytest.mark.parametrize("npts", ["33", "65"])
-def test_printed_semi_unbounded(npts):
+@pytest.mark.parametrize("kernel", ["hej2", "hej4", "hej6", "hej8", "hej10", "hej0"])
+def test_printed_semi_unbounded(kernel, npts):
     N = int(npts) - 1
     phi, f = analytic.case_semi_unbounded(N)
     h = 1.0 / N
-    p = Problem(bc=((UNB, EVEN), (UNB, UNB), (ODD, UNB)), h=(h, h, h), center=NODE, kernel="hej2")
+    p = Problem(bc=((UNB, EVEN), (UNB, UNB), (ODD, UNB)), h=(h, h, h), center=NODE, kernel=kernel)
     err = np.abs(solve(f, p) - phi).max()
-    _check_printed(err, _G["semi_unbounded"]["hej2"][npts])
+    _check_printed(err, _G["semi_unbounded"][kernel][npts])
 
 
 # ---------------------------------------------------------------------------
@@ -252,6 +254,59 @@ def test_hej2_2d_far_field_and_zero_mode():
         assert abs(lim - g0) < 1e-7
     g0 = green.hej2_2d(np.array([0.0]), np.array([1.5]), EPS)[0]
     assert abs(g0 - math.log(1.5) / (2 * math.pi)) < 1e-14
+
+
+def _spectral_hej(m, k):
+    """The fully spectral HEJ2m kernel -exp(-s) sum_{j<m} s^j/j! / k^2, s = k^2 eps^2/2 (its definition)."""
+    s = k * k * EPS * EPS / 2
+    acc, term = 0.0, 1.0
+    for j in range(m):
+        if j > 0:
+            term *= s / j
+        acc += term
+    return -math.exp(-s) * acc / (k * k)
+
+
+@pytest.mark.parametrize("m", [2, 3, 4, 5])
+@pytest.mark.parametrize("r", [0.0, 0.004, 0.05, 0.1, 0.3, 0.9])
+def test_hej_higher_order_3d_against_inverse_transform(m, r):
+    """d_u = 3: G(r) = (1/(2 pi^2 r)) int_0^inf G^(k) k sin(k r) dk (radial inverse Fourier transform
+    of the spectral definition); at r = 0 the integrand is G^(k) k^2 / (2 pi^2)."""
+    if r == 0.0:
+        fn = lambda k: _spectral_hej(m, k) * k * k / (2 * math.pi ** 2)
+    else:
+        fn = lambda k: _spectral_hej(m, k) * k * math.sin(k * r) / (2 * math.pi ** 2 * r)
+    q, _ = integrate.quad(fn, 0.0, 60.0 / EPS, limit=4000, epsabs=0, epsrel=1e-13)
+    g = green.hej_mixed(m, 3, np.array([0.0]), np.array([r]), EPS)[0]
+    assert abs(g - q) <= 1e-12 * abs(q)
+
+
+@pytest.mark.parametrize("m", [2, 3, 5])
+@pytest.mark.parametrize("k,z", [(1.0, 0.0), (3.0, 0.2), (30.0, 0.05), (0.5, 0.7)])
+def test_hej_higher_order_1d_against_inverse_transform(m, k, z):
+    """d_u = 1: G(k_s, z) = (1/pi) int_0^inf G^(sqrt(k_s^2 + w^2)) cos(w z) dw."""
+    fn = lambda w: _spectral_hej(m, math.sqrt(k * k + w * w)) * math.cos(w * z) / math.pi
+    q, _ = integrate.quad(fn, 0.0, 60.0 / EPS, limit=4000, epsabs=0, epsrel=1e-13)
+    g = green.hej_mixed(m, 1, np.array([k]), np.array([z]), EPS)[0]
+    assert abs(g - q) <= 1e-11 * abs(q)
+
+
+@pytest.mark.parametrize("m", [2, 4, 5])
+@pytest.mark.parametrize("k,r", [(1.0, 0.0), (3.0, 0.2), (30.0, 0.05), (0.5, 0.7)])
+def test_hej_higher_order_2d_against_inverse_transform(m, k, r):
+    """d_u = 2: G(k_s, r) = (1/(2 pi)) int_0^inf G^(sqrt(k_s^2 + w^2)) J0(w r) w dw."""
+    fn = lambda w: _spectral_hej(m, math.sqrt(k * k + w * w)) * special.j0(w * r) * w / (2 * math.pi)
+    q, _ = integrate.quad(fn, 0.0, 60.0 / EPS, limit=4000, epsabs=0, epsrel=1e-13)
+    g = green.hej_mixed(m, 2, np.array([k]), np.array([r]), EPS)[0]
+    assert abs(g - q) <= 1e-11 * abs(q)
+
+
+def test_hej_higher_order_reduces_to_hej2():
+    k = np.array([0.0, 2.0, 7.0])
+    r = np.array([0.1, 0.0, 0.3])
+    for du in (1, 2, 3):
+        kk = np.zeros(3) if du == 3 else k
+        assert np.array_equal(green.hej_mixed(1, du, kk, r, EPS), green.hej2_mixed(du, kk, r, EPS))
 
 
 def test_hej2_3d_and_hej0_limits():
