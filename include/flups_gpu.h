@@ -60,8 +60,8 @@ typedef enum { FLUPS_F32 = 0, FLUPS_F64 = 1, FLUPS_F64E = 2 } flups_prec;
 typedef enum { FLUPS_POISSON = 0, FLUPS_BIOT_SAVART = 1 } flups_op;
 /* Green kernels (Section "Validation").  SPECTRAL is -1/|k|^2 with the zero
  * mode set to 0 (spectral/periodic BCs only).  HEJ2..HEJ10: regularised of
- * order 2m, eps = eps_over_h * max(h); HEJ4..HEJ10 on spectral BCs only.
- * HEJ0: spectral truncation at pi/h, fully unbounded only.  LGF2: lattice
+ * order 2m, eps = eps_over_h * max(h), with any boundary conditions.
+ * HEJ0: spectral truncation at pi/h, every direction unbounded or semi-unbounded.  LGF2: lattice
  * Green's function, spectral BCs only. */
 typedef enum {
   FLUPS_SPECTRAL = 0, FLUPS_HEJ0 = 1, FLUPS_HEJ2 = 2, FLUPS_HEJ4 = 4, FLUPS_HEJ6 = 6,
@@ -233,7 +233,9 @@ const char* flups_last_cuda_error(void);
 /* Test hook: evaluate the device FP64 special functions used by the Green's
  * function generation at n points (device arrays x, y, out): which = 0 E1(x),
  * 1 Si(x), 2 HEJ2 one-unbounded kernel G(k = x, z = y), 3 two-unbounded
- * kernel G(k = x, r = y), 4 three-unbounded kernel G(r = y).  Synchronous. */
+ * kernel G(k = x, r = y), 4 three-unbounded kernel G(r = y), 10 d_u + m
+ * (d_u = 1..3, m = 2..5) the terms that turn the HEJ2 kernel with d_u unbounded
+ * directions into HEJ2m, at k_s = x, r = y.  Synchronous. */
 int flups_debug_special(int which, const double* x, const double* y, double* out, int n, double eps);
 
 #ifdef __cplusplus

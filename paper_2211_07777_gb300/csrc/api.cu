@@ -444,6 +444,7 @@ int setup_green(flups_solver_s* s, cudaStream_t st) {
   }
   q.du = du;
   q.kernel = s->green == FLUPS_HEJ0 ? 1 : 0;
+  q.hej_m = (s->green >= FLUPS_HEJ2 && s->green <= FLUPS_HEJ10) ? s->green / 2 : 1;
   q.eps = s->eps;
   q.hmax = std::fmax(s->h[0], std::fmax(s->h[1], s->h[2]));
   gauss_legendre(GL_N, q.gl_x, q.gl_w);
@@ -813,7 +814,8 @@ int flups_init_solver(flups_topo t, const int* bc, const double h[3], const doub
     int du = 0;
     for (int d = 0; d < 3; ++d) du += s->dir[d].unb;
     if (du == 0 && green == FLUPS_HEJ0) rc = FLUPS_EGREEN;
-    if (du > 0 && !(green == FLUPS_HEJ2 || (green == FLUPS_HEJ0 && du == 3))) rc = FLUPS_EGREEN;
+    const bool hej2m = green >= FLUPS_HEJ2 && green <= FLUPS_HEJ10;
+    if (du > 0 && !(hej2m || (green == FLUPS_HEJ0 && du == 3))) rc = FLUPS_EGREEN;
   }
   if (rc != FLUPS_OK) {
     delete s;

@@ -161,6 +161,45 @@ __device__ double hej2_du2(double k, double r, double eps, const GreenSamplePara
   return -acc / (4.0 * PI_D);
 }
 
+// Order 2m kernels (m >= 2) from the order-2 one: the spectral HEJ2m kernel is
+// -int_a^inf t^{m-1} |k|^{2(m-1)} e^{-t|k|^2} dt/(m-1)!  (a = eps^2/2), and
+// |k|^{2n} e^{-t|k|^2} = (-d/dt)^n e^{-t|k|^2}; over the unbounded directions
+// e^{-t|k|^2} becomes the heat kernel H(t) = e^{-t k_s^2}(4 pi t)^{-d_u/2} e^{-r^2/(4t)}.
+// m - 1 integrations by parts leave
+//     G_2m = G_2 + sum_{j=1}^{m-1} (-1)^j a^j H^{(j-1)}(a) / j!.
+// The derivatives of H come from its logarithmic derivative
+//     Lg(t) = (ln H)' = -k_s^2 - (d_u/2)/t + (r^2/4)/t^2,
+//     Lg^{(p)}(t) = (-1)^p [-(d_u/2) p! t^{-p-1} + (r^2/4)(p+1)! t^{-p-2}],  p >= 1,
+// and H^{(n+1)} = sum_{i<=n} C(n, i) H^{(i)} Lg^{(n-i)}.
+__device__ double hej_higher_order_terms(int m, double k, double r, int du, double eps) {
+  const double a = 0.5 * eps * eps;
+  const double b = 0.25 * r * r, half_du = 0.5 * du;
+  double H[5], Lg[4];
+  H[0] = exp(-a * k * k - b / a) * pow(4.0 * PI_D * a, -half_du);
+  Lg[0] = -k * k - half_du / a + b / (a * a);
+  double fact = 1.0, sgn = -1.0;
+  for (int p = 1; p < 4; ++p) {
+    fact *= p;  // p!
+    Lg[p] = sgn * (-half_du * fact * pow(a, -p - 1) + b * fact * (p + 1) * pow(a, -p - 2));
+    sgn = -sgn;
+  }
+  for (int n = 0; n + 1 < m - 1; ++n) {
+    double acc = 0.0, binom = 1.0;
+    for (int i = 0; i <= n; ++i) {
+      acc += binom * H[i] * Lg[n - i];
+      binom = binom * (n - i) / (i + 1);
+    }
+    H[n + 1] = acc;
+  }
+  double out = 0.0, aj = 1.0, jfact = 1.0;
+  for (int j = 1; j < m; ++j) {
+    aj *= a;
+    jfact *= j;
+    out += ((j & 1) ? -1.0 : 1.0) * aj * H[j - 1] / jfact;
+  }
+  return out;
+}
+
 __global__ void k_green_sample(double* __restrict__ g, GreenSampleParams q) {
   const long long tot = (long long)q.gext[0] * q.gext[1] * q.gext[2];
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
@@ -186,6 +225,7 @@ __global__ void k_green_sample(double* __restrict__ g, GreenSampleParams q) {
     else if (q.du == 3) v = hej2_du3(r, q.eps);
     else if (q.du == 2) v = hej2_du2(k, r, q.eps, q);
     else v = hej2_du1(k, r, q.eps);
+    if (q.kernel == 0 && q.hej_m > 1) v += hej_higher_order_terms(q.hej_m, k, r, q.du, q.eps);
     g[idx] = v;
   }
 }
@@ -274,7 +314,13 @@ __global__ void k_special_eval(int which, const double* __restrict__ x, const do
     case 2: out[i] = hej2_du1(x[i], y[i], eps); break;
     case 3: out[i] = hej2_du2(x[i], y[i], eps, q); break;
     case 4: out[i] = hej2_du3(y[i], eps); break;
-    default: out[i] = 0.0; break;
+    default:
+      // 10 d_u + m (m = 2..5): the order-2m correction terms with d_u unbounded directions
+      if (which >= 12 && which <= 35 && which % 10 >= 2 && which % 10 <= 5)
+        out[i] = hej_higher_order_terms(which % 10, x[i], y[i], which / 10, eps);
+      else
+        out[i] = 0.0;
+      break;
   }
 }
 

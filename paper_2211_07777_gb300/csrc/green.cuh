@@ -13,7 +13,8 @@ struct GreenSampleParams {
   double wscale[3];   // spectral wavenumber w = wscale (g + wshift)
   double wshift[3];
   int du;             // number of unbounded-like directions
-  int kernel;         // 0 HEJ2, 1 HEJ0
+  int kernel;         // 0 HEJ2m (order 2m, m = hej_m), 1 HEJ0
+  int hej_m;          // m of HEJ2m (1 ... 5)
   double eps;         // regularisation length
   double hmax;        // HEJ0 cut-off spacing
   double gl_x[GL_N];  // Gauss-Legendre nodes and weights on [-1, 1]

@@ -65,7 +65,7 @@ def test_host_validation(lib):
         _solver(F, (16, 16, 16), ((U, U), (P, P), (P, P)), green="spectral")   # singular kernel, unbounded
     assert e.value.status == -6
     with pytest.raises(F.FlupsError) as e:
-        _solver(F, (16, 16, 16), ((U, U), (E, O), (P, P)), green="hej4")
+        _solver(F, (16, 16, 16), ((U, U), (E, O), (P, P)), green="lgf2")
     assert e.value.status == -6
     with pytest.raises(F.FlupsError) as e:
         _solver(F, (4096, 16, 16), ((E, O), (P, P), (P, P)))          # 4N > 4096
