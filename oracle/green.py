@@ -33,6 +33,9 @@ convergence tables and against independent quadrature:
   (the terms at t = inf vanish for k_s > 0 or d_u = 3).
 * HEJ0 (fully unbounded, spectral truncation of the kernel at |k| = pi/h):
   G = -Si(pi r / h)/(2 pi^2 r),  G(0) = -1/(2 pi h).
+* LGF2 with every direction unbounded: the lattice Green's function of the
+  7-point Laplacian, as an integral of products of scaled modified Bessel
+  functions (lgf_3d).
 """
 from __future__ import annotations
 
@@ -239,3 +242,72 @@ def hej_mixed(m: int, du: int, kmag: np.ndarray, r: np.ndarray, eps: float) -> n
     for j in range(1, m):
         g = g + (-1.0) ** j * a ** j * hd[j - 1] / math.factorial(j)
     return g
+
+
+# ---------------------------------------------------------------------------
+# Lattice Green's function (LGF2) with every direction unbounded.
+# ---------------------------------------------------------------------------
+def _ive_series_coeffs(nu: np.ndarray, J: int):
+    """a_j(nu), j < J, of the large-x expansion e^{-x} I_nu(x) ~ (2 pi x)^{-1/2} sum_j (-1)^j a_j / x^j,
+    a_j = prod_{i=1..j} (4 nu^2 - (2i-1)^2) / (j! 8^j)."""
+    mu = 4.0 * np.asarray(nu, dtype=np.float64) ** 2
+    out = [np.ones_like(mu)]
+    for j in range(1, J):
+        out.append(out[-1] * (mu - (2 * j - 1) ** 2) / (j * 8.0))
+    return out
+
+
+def lgf_3d(n0, n1, n2, h) -> np.ndarray:
+    """Lattice Green's function of the 7-point Laplacian sum_d (u(n+e_d) - 2u(n) + u(n-e_d))/h_d^2
+    with a unit source 1/(h0 h1 h2) at the origin, at integer offsets (n0, n1, n2):
+
+        G(n) = -(1/(h0 h1 h2)) int_0^inf prod_d e^{-2t/h_d^2} I_{n_d}(2t/h_d^2) dt
+
+    (1/sigma(theta) = int_0^inf e^{-t sigma} dt and (1/2pi) int e^{i n theta} e^{2s cos theta} dtheta = I_n(2s)).
+    Quadrature: t = hmin^2 s; Gauss-Legendre on s in [0, 1], on panels of width 1/4 in ln s up to T,
+    and beyond T the large-argument expansion of each factor integrated term by term."""
+    n = [np.abs(np.asarray(v, dtype=np.int64)) for v in (n0, n1, n2)]
+    n = np.broadcast_arrays(*n)
+    hmin = min(h)
+    c = [hmin * hmin / (hd * hd) for hd in h]
+    nmax = [int(v.max()) if v.size else 0 for v in n]
+    T = max(1.0e4, max(100.0 * (nm * nm + 1) / cd for nm, cd in zip(nmax, c)))
+    x16, w16 = np.polynomial.legendre.leggauss(16)
+    nodes, weights = [], []
+    for lo, hi in ((0.0, 0.5), (0.5, 1.0)):
+        nodes.append(lo + (hi - lo) * (x16 + 1) / 2)
+        weights.append((hi - lo) / 2 * w16)
+    npan = int(math.ceil(math.log(T) / 0.25))
+    du = math.log(T) / npan
+    for p in range(npan):
+        u = p * du + du * (x16 + 1) / 2
+        s = np.exp(u)
+        nodes.append(s)
+        weights.append(du / 2 * w16 * s)
+    s = np.concatenate(nodes)
+    w = np.concatenate(weights)
+    B = [special.ive(np.arange(nm + 1)[:, None], 2.0 * cd * s[None, :]) for nm, cd in zip(nmax, c)]
+    flat = [v.ravel() for v in n]
+    F = np.empty(flat[0].shape, dtype=np.float64)
+    chunk = 4096
+    for i in range(0, F.size, chunk):
+        sl = slice(i, i + chunk)
+        F[sl] = (B[0][flat[0][sl]] * B[1][flat[1][sl]] * B[2][flat[2][sl]]) @ w
+    # tail: prod_d (4 pi c_d s)^{-1/2} sum_j (-1)^j a_j(n_d) (2 c_d s)^{-j}, integrated over s > T
+    J = 6
+    poly = np.ones((F.size, 1))
+    for d in range(3):
+        a = _ive_series_coeffs(flat[d], J)
+        fac = np.stack([(-1.0) ** j * a[j] * (2.0 * c[d]) ** (-j) for j in range(J)], axis=1)
+        prod = np.zeros((F.size, poly.shape[1] + J - 1))
+        for j in range(J):
+            prod[:, j:j + poly.shape[1]] += fac[:, j:j + 1] * poly
+        poly = prod[:, :J]
+    K = 1.0
+    for cd in c:
+        K /= math.sqrt(4.0 * math.pi * cd)
+    tail = np.zeros(F.size)
+    for j in range(J):
+        tail += poly[:, j] * T ** (-0.5 - j) / (0.5 + j)
+    F += K * tail
+    return (-(hmin * hmin) / (h[0] * h[1] * h[2]) * F).reshape(n[0].shape)

@@ -243,6 +243,13 @@ def green_spectrum(prob: Problem, shape_ext) -> np.ndarray:
         g = _green.hej_mixed(int(prob.kernel[3:]) // 2, du, kmag, r, prob.eps)
     elif prob.kernel == "hej0" and du == 3:
         g = _green.hej0_3d(r, max(prob.h))
+    elif prob.kernel == "lgf2" and du == 3:
+        # evaluate on the folded offsets 0..P_d/2, then unfold (the samples are even in every direction)
+        off = [np.minimum(np.arange(P[d]), P[d] - np.arange(P[d])) for d in range(3)]
+        fold = [bcast(np.arange(P[d] // 2 + 1), d) for d in range(3)]
+        fold = np.broadcast_arrays(*fold)
+        gf = _green.lgf_3d(fold[0], fold[1], fold[2], prob.h)
+        g = gf[np.ix_(off[2], off[1], off[0])]
     else:
         raise ValueError(f"kernel {prob.kernel!r} with {du} unbounded direction(s) is not in the oracle")
     axes = tuple(2 - d for d in unb)

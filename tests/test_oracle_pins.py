@@ -174,7 +174,7 @@ def test_printed_symmetric_periodic(kernel, npts):
 
 
 @pytest.mark.parametrize("npts", ["33", "65"])
-@pytest.mark.parametrize("kernel", ["hej2", "hej4", "hej6", "hej8", "hej10", "hej0"])
+@pytest.mark.parametrize("kernel", ["lgf2", "hej2", "hej4", "hej6", "hej8", "hej10", "hej0"])
 def test_printed_unbounded(kernel, npts):
     N = int(npts) - 1
     phi, f = analytic.case_unbounded(N)
@@ -185,7 +185,7 @@ def test_printed_unbounded(kernel, npts):
 
 
 @pytest.mark.parametrize("npts", ["33", "65"])
-@pytest.mark.parametrize("kernel", ["hej2", "hej4", "hej6", "hej8", "hej10", "hej0"])
+@pytest.mark.parametrize("kernel", ["lgf2", "hej2", "hej4", "hej6", "hej8", "hej10", "hej0"])
 def test_printed_semi_unbounded(kernel, npts):
     N = int(npts) - 1
     phi, f = analytic.case_semi_unbounded(N)
@@ -307,6 +307,63 @@ def test_hej_higher_order_reduces_to_hej2():
     for du in (1, 2, 3):
         kk = np.zeros(3) if du == 3 else k
         assert np.array_equal(green.hej_mixed(1, du, kk, r, EPS), green.hej2_mixed(du, kk, r, EPS))
+
+
+def test_lattice_green_origin_is_watson_constant():
+    """G(0) h = -W/6 with Watson's simple-cubic integral W = (1/pi^3) int_[0,pi]^3 dtheta/(1 - sum cos/3)
+    in its closed form sqrt(6)/(32 pi^3) Gamma(1/24) Gamma(5/24) Gamma(7/24) Gamma(11/24) (Glasser and
+    Zucker): 1/sum_d (2 - 2 cos theta_d) = 1/(6 (1 - sum cos/3))."""
+    W = math.sqrt(6) / (32 * math.pi ** 3) * math.gamma(1 / 24) * math.gamma(5 / 24) * math.gamma(7 / 24) \
+        * math.gamma(11 / 24)
+    for h in (1.0, 0.25):
+        g0 = green.lgf_3d(np.array([0]), np.array([0]), np.array([0]), (h, h, h))[0]
+        assert abs(g0 * h + W / 6) < 1e-15
+
+
+@pytest.mark.parametrize("h", [(1.0, 1.0, 1.0), (1.0, 0.7, 1.3)])
+def test_lattice_green_is_discrete_fundamental_solution(h):
+    """The 7-point Laplacian of G is 1/(h0 h1 h2) at the origin and 0 everywhere else."""
+    n = 10
+    i = np.arange(-n, n + 1)
+    Z, Y, X = np.meshgrid(i, i, i, indexing="ij")
+    G = green.lgf_3d(X, Y, Z, h)
+    c = G[1:-1, 1:-1, 1:-1]
+    lap = (G[1:-1, 1:-1, 2:] + G[1:-1, 1:-1, :-2] - 2 * c) / h[0] ** 2 \
+        + (G[1:-1, 2:, 1:-1] + G[1:-1, :-2, 1:-1] - 2 * c) / h[1] ** 2 \
+        + (G[2:, 1:-1, 1:-1] + G[:-2, 1:-1, 1:-1] - 2 * c) / h[2] ** 2
+    vol = h[0] * h[1] * h[2]
+    m = n - 1
+    assert abs(lap[m, m, m] * vol - 1.0) < 1e-13
+    lap[m, m, m] = 0.0
+    assert np.abs(lap).max() * vol < 1e-13
+
+
+@pytest.mark.parametrize("n", [(0, 0, 5), (10, 3, 2), (32, 32, 32), (64, 0, 1)])
+def test_lattice_green_against_adaptive_quadrature(n):
+    """The defining integral -int_0^inf prod_d e^{-2t} I_{n_d}(2t) dt by adaptive quadrature up to
+    10^6 plus the termwise tail, independent of the oracle's fixed-node rule."""
+    fn = lambda t: special.ive(n[0], 2 * t) * special.ive(n[1], 2 * t) * special.ive(n[2], 2 * t)
+    pts = [0, 0.5, 1, 3, 10, 30, 100, 300, 1e3, 3e3, 1e4, 3e4, 1e5, 3e5, 1e6]
+    q = sum(integrate.quad(fn, a, b, limit=400, epsabs=0, epsrel=1e-13)[0] for a, b in zip(pts[:-1], pts[1:]))
+    # beyond T = 10^6: product of the three large-x series of e^{-x} I_k(x), x = 2t, integrated termwise
+    ser = []
+    for k in n:
+        c, term = [1.0], 1.0
+        for j in range(1, 6):
+            term *= -(4 * k * k - (2 * j - 1) ** 2) / (8 * j)
+            c.append(term)
+        ser.append(np.array(c))
+    prod = np.convolve(np.convolve(ser[0], ser[1]), ser[2])[:6]
+    T = 1e6
+    q += (4 * math.pi) ** -1.5 * sum(cj * 2.0 ** -j * T ** (-0.5 - j) / (0.5 + j) for j, cj in enumerate(prod))
+    g = green.lgf_3d(np.array([n[0]]), np.array([n[1]]), np.array([n[2]]), (1.0, 1.0, 1.0))[0]
+    assert abs(g + q) < 1e-12 * q
+
+
+def test_lattice_green_far_field():
+    """|n| -> inf: G -> -1/(4 pi |n| h) (the continuous fundamental solution)."""
+    g = green.lgf_3d(np.array([200]), np.array([0]), np.array([0]), (1.0, 1.0, 1.0))[0]
+    assert abs(g * 4 * math.pi * 200 + 1) < 1e-5
 
 
 def test_hej2_3d_and_hej0_limits():
