@@ -242,6 +242,7 @@ void gauss_legendre(int n, double* x, double* w) {
   }
 }
 
+
 ArrDesc arr_desc(const int* d, int axis) {
   ArrDesc a{};
   const long long tot = (long long)d[0] * d[1] * d[2];
@@ -450,7 +451,7 @@ int setup_green(flups_solver_s* s, cudaStream_t st) {
   gauss_legendre(GL_N, q.gl_x, q.gl_w);
   double* g64 = nullptr;
   CK(cudaMallocAsync(&g64, n * sizeof(double), st));
-  cudaError_t e = launch_green_sample(g64, q, st);
+  cudaError_t e = (s->green == FLUPS_LGF2) ? launch_lgf(g64, q.gext, q.h, st) : launch_green_sample(g64, q, st);
   if (e) { cudaFreeAsync(g64, st); return cuda_fail(e, "green sample"); }
   double vol = 1.0;
   for (int d = 0; d < 3; ++d) {
@@ -699,6 +700,10 @@ cudaError_t g_limits_err = cudaSuccess;
 
 }  // namespace
 
+namespace flups {
+void host_gauss_legendre(int n, double* x, double* w) { gauss_legendre(n, x, w); }
+}  // namespace flups
+
 extern "C" {
 
 const char* flups_strerror(int status) {
@@ -815,7 +820,7 @@ int flups_init_solver(flups_topo t, const int* bc, const double h[3], const doub
     for (int d = 0; d < 3; ++d) du += s->dir[d].unb;
     if (du == 0 && green == FLUPS_HEJ0) rc = FLUPS_EGREEN;
     const bool hej2m = green >= FLUPS_HEJ2 && green <= FLUPS_HEJ10;
-    if (du > 0 && !(hej2m || (green == FLUPS_HEJ0 && du == 3))) rc = FLUPS_EGREEN;
+    if (du > 0 && !(hej2m || ((green == FLUPS_HEJ0 || green == FLUPS_LGF2) && du == 3))) rc = FLUPS_EGREEN;
   }
   if (rc != FLUPS_OK) {
     delete s;

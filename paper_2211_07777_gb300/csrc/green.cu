@@ -230,6 +230,201 @@ __global__ void k_green_sample(double* __restrict__ g, GreenSampleParams q) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Lattice Green's function of the 7-point Laplacian (LGF2, every direction
+// unbounded-like), with a unit source 1/(h0 h1 h2):
+//     G(n) = -(1/(h0 h1 h2)) int_0^inf prod_d e^{-2t/h_d^2} I_{n_d}(2t/h_d^2) dt
+// (1/sigma = int_0^inf e^{-t sigma} dt applied to the lattice symbol, and the
+// generating function of I_n).  With t = hmin^2 s and c_d = hmin^2/h_d^2 the
+// integrand is prod_d E(n_d, 2 c_d s), E(n, x) = e^{-x} I_n(x).  The integral
+// is a fixed quadrature sum_q w_q prod_d E(n_d, 2 c_d s_q) up to s = T, plus the
+// termwise integral of the large-argument expansion beyond T; the per-direction
+// tables E(n, 2 c_d s_q), n = 0..nmax, make every sample a short dot product.
+// ---------------------------------------------------------------------------
+
+// a_j(n) (2c)^{-j} of e^{-x} I_n(x) ~ (2 pi x)^{-1/2} sum_j (-1)^j a_j(n) x^{-j}, x = 2 c s, as powers of 1/s
+__device__ __forceinline__ void lgf_series(int n, double c, int J, double* out) {
+  const double mu = 4.0 * (double)n * n;
+  double a = 1.0;
+  out[0] = 1.0;
+  for (int j = 1; j < J; ++j) {
+    a *= -(mu - (2.0 * j - 1.0) * (2.0 * j - 1.0)) / (8.0 * j * 2.0 * c);
+    out[j] = a;
+  }
+}
+
+// Table row of node q: E(n, x), n = 0..nmax, x = 2 c s_q, stored at B[q (nmax + 1) + n].
+__global__ void k_lgf_table(double* __restrict__ B, const double* __restrict__ sq, int Q, int nmax, double c) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  double* row = B + (size_t)q * (nmax + 1);
+  const double x = 2.0 * c * sq[q];
+  if (x < 1.0) {
+    // power series e^{-x} sum_k (x/2)^{2k+n} / (k! (k+n)!)
+    const double ex = exp(-x), y = 0.25 * x * x;
+    double lead = 1.0;  // (x/2)^n / n!
+    for (int n = 0; n <= nmax; ++n) {
+      double sum = 0.0, term = 1.0;
+      for (int k = 0; k < 40; ++k) {
+        if (k > 0) term *= y / ((double)k * (k + n));
+        sum += term;
+        if (term < 1e-18 * sum) break;
+      }
+      row[n] = ex * lead * sum;
+      lead *= 0.5 * x / (n + 1);
+    }
+    return;
+  }
+  if (x > 50.0 * ((double)nmax * nmax + 1.0) && x > 400.0) {
+    // large argument: (2 pi x)^{-1/2} sum_j (-1)^j a_j(n) / x^j, terms shrink at least 100x each
+    const double pre = rsqrt(2.0 * PI_D * x);
+    for (int n = 0; n <= nmax; ++n) {
+      const double mu = 4.0 * (double)n * n;
+      double term = 1.0, sum = 1.0;
+      for (int j = 1; j < 12; ++j) {
+        term *= -(mu - (2.0 * j - 1.0) * (2.0 * j - 1.0)) / (8.0 * j * x);
+        sum += term;
+        if (fabs(term) < 1e-18 * fabs(sum)) break;
+      }
+      row[n] = pre * sum;
+    }
+    return;
+  }
+  // Miller's backward recurrence I_{n-1} = I_{n+1} + (2n/x) I_n from far above nmax (where
+  // I_n(x)/I_0(x) ~ exp(-n^2/(2x)) is negligible), normalised by e^{-x}(I_0 + 2 sum_{n>=1} I_n) = 1
+  const int ns = nmax + 24 + (int)(10.0 * sqrt(x));
+  const double ix = 1.0 / x;
+  double up = 0.0, cur = 1e-280, sum = 0.0;
+  for (int n = ns; n >= 1; --n) {
+    const double dn = up + 2.0 * n * ix * cur;  // I_{n-1}
+    sum += 2.0 * cur;                             // I_n, n >= 1
+    if (n <= nmax) row[n] = cur;
+    up = cur;
+    cur = dn;
+    if (fabs(cur) > 1e250) {
+      up *= 1e-250;
+      cur *= 1e-250;
+      sum *= 1e-250;
+      for (int m = n; m <= nmax; ++m) row[m] *= 1e-250;
+    }
+  }
+  sum += cur;
+  row[0] = cur;
+  const double inv = 1.0 / sum;
+  for (int n = 0; n <= nmax; ++n) row[n] *= inv;
+}
+
+struct LgfParams {
+  int gext[3];
+  int nmax[3];
+  const double* B[3];   // per-direction tables [Q][nmax + 1]
+  const double* w;      // quadrature weights (ds)
+  int Q;
+  double T;             // quadrature end; the tail beyond is integrated termwise
+  double c[3];          // hmin^2 / h_d^2
+  double scale;         // -hmin^2 / (h0 h1 h2)
+};
+
+__global__ void k_lgf_sample(double* __restrict__ g, LgfParams p) {
+  const long long tot = (long long)p.gext[0] * p.gext[1] * p.gext[2];
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % p.gext[0]);
+    const long long rest = idx / p.gext[0];
+    const int j = (int)(rest % p.gext[1]), k = (int)(rest / p.gext[1]);
+    const double* b0 = p.B[0] + i;
+    const double* b1 = p.B[1] + j;
+    const double* b2 = p.B[2] + k;
+    const int s0 = p.nmax[0] + 1, s1 = p.nmax[1] + 1, s2 = p.nmax[2] + 1;
+    double acc = 0.0;
+    for (int q = 0; q < p.Q; ++q) acc += p.w[q] * b0[(size_t)q * s0] * b1[(size_t)q * s1] * b2[(size_t)q * s2];
+    // tail: prod_d (4 pi c_d s)^{-1/2} (sum_j A_dj s^{-j}) over s > T
+    constexpr int J = 7;
+    double a0[J], a1[J], a2[J], c01[J];
+    lgf_series(i, p.c[0], J, a0);
+    lgf_series(j, p.c[1], J, a1);
+    lgf_series(k, p.c[2], J, a2);
+    for (int m = 0; m < J; ++m) {
+      c01[m] = 0.0;
+      for (int l = 0; l <= m; ++l) c01[m] += a0[l] * a1[m - l];
+    }
+    double tail = 0.0, tp = rsqrt(p.T);
+    for (int m = 0; m < J; ++m) {
+      double cm = 0.0;
+      for (int l = 0; l <= m; ++l) cm += c01[l] * a2[m - l];
+      tail += cm * tp / (0.5 + m);
+      tp /= p.T;
+    }
+    tail *= rsqrt(64.0 * PI_D * PI_D * PI_D * p.c[0] * p.c[1] * p.c[2]);
+    g[idx] = p.scale * (acc + tail);
+  }
+}
+
+cudaError_t launch_lgf(double* g, const int* gext, const double* h, cudaStream_t st) {
+  // quadrature in s: one 32-node Gauss-Legendre panel on [0, 2], then 16-node panels of width 1/3 in ln s
+  double x32[32], w32[32], x16[16], w16[16];
+  host_gauss_legendre(32, x32, w32);
+  host_gauss_legendre(16, x16, w16);
+  const double hmin = fmin(h[0], fmin(h[1], h[2]));
+  double c[3], T = 1e5;
+  int nmax[3];
+  for (int d = 0; d < 3; ++d) {
+    c[d] = hmin * hmin / (h[d] * h[d]);
+    nmax[d] = gext[d] - 1;
+    T = fmax(T, 400.0 * ((double)nmax[d] * nmax[d] + 1.0) / c[d]);
+  }
+  const double u0 = log(2.0), u1 = log(T);
+  const int npan = (int)ceil((u1 - u0) * 3.0);
+  const double du = (u1 - u0) / npan;
+  const int Q = 32 + 16 * npan;
+  double* hs = (double*)malloc(2 * sizeof(double) * Q);
+  if (!hs) return cudaErrorMemoryAllocation;
+  double* hw = hs + Q;
+  for (int i = 0; i < 32; ++i) {
+    hs[i] = 1.0 + x32[i];
+    hw[i] = w32[i];
+  }
+  for (int pn = 0; pn < npan; ++pn)
+    for (int i = 0; i < 16; ++i) {
+      const double u = u0 + du * (pn + 0.5 * (x16[i] + 1.0));
+      const double sv = exp(u);
+      hs[32 + 16 * pn + i] = sv;
+      hw[32 + 16 * pn + i] = 0.5 * du * w16[i] * sv;
+    }
+  size_t tab = 0;
+  for (int d = 0; d < 3; ++d) tab += (size_t)Q * (nmax[d] + 1);
+  double* dev = nullptr;
+  cudaError_t e = cudaMallocAsync(&dev, (2 * (size_t)Q + tab) * sizeof(double), st);
+  if (e) { free(hs); return e; }
+  e = cudaMemcpyAsync(dev, hs, 2 * sizeof(double) * Q, cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  free(hs);
+  LgfParams p{};
+  double* t = dev + 2 * (size_t)Q;
+  for (int d = 0; d < 3 && !e; ++d) {
+    p.gext[d] = gext[d];
+    p.nmax[d] = nmax[d];
+    p.c[d] = c[d];
+    p.B[d] = t;
+    k_lgf_table<<<(Q + 63) / 64, 64, 0, st>>>(t, dev, Q, nmax[d], c[d]);
+    e = cudaGetLastError();
+    t += (size_t)Q * (nmax[d] + 1);
+  }
+  if (!e) {
+    p.w = dev + Q;
+    p.Q = Q;
+    p.T = T;
+    p.scale = -hmin * hmin / (h[0] * h[1] * h[2]);
+    const long long tot = (long long)gext[0] * gext[1] * gext[2];
+    long long blocks = (tot + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_lgf_sample<<<(unsigned)blocks, 256, 0, st>>>(g, p);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(dev, st);
+  return e;
+}
+
 template <typename T>
 __global__ void k_green_finalize(const double* __restrict__ g, T* __restrict__ out, long long n, double scale) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)

@@ -22,6 +22,10 @@ struct GreenSampleParams {
 };
 
 cudaError_t launch_green_sample(double* g, const GreenSampleParams& q, cudaStream_t st);
+// Lattice Green's function samples G(n), n_d = 0..gext[d]-1 (every direction unbounded-like).
+cudaError_t launch_lgf(double* g, const int* gext, const double* h, cudaStream_t st);
+// n-point Gauss-Legendre nodes and weights on [-1, 1] (host).
+void host_gauss_legendre(int n, double* x, double* w);
 cudaError_t launch_green_finalize(const double* g, void* out, int prec, long long n, double scale, cudaStream_t st);
 cudaError_t launch_green_spectral(double* g, const int* gext, const double* const* tabs, int kernel, double eps2h,
                                   double scale, cudaStream_t st);

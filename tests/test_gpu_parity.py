@@ -129,7 +129,7 @@ def _printed_tol(kernel):
     return 1e-7 if kernel == "hej0" else 1e-10
 
 
-@pytest.mark.parametrize("kernel", ["hej2", "hej4", "hej6", "hej8", "hej10", "hej0"])
+@pytest.mark.parametrize("kernel", ["lgf2", "hej2", "hej4", "hej6", "hej8", "hej10", "hej0"])
 def test_printed_unbounded_on_gpu(kernel):
     N = 32
     phi, f = analytic.case_unbounded(N)
@@ -139,7 +139,7 @@ def test_printed_unbounded_on_gpu(kernel):
     assert abs(err - want) < _printed_tol(kernel) * want, (err, want)
 
 
-@pytest.mark.parametrize("kernel", ["hej2", "hej4", "hej6", "hej8", "hej10", "hej0"])
+@pytest.mark.parametrize("kernel", ["lgf2", "hej2", "hej4", "hej6", "hej8", "hej10", "hej0"])
 def test_printed_semi_unbounded_on_gpu(kernel):
     N = 32
     phi, f = analytic.case_semi_unbounded(N)
@@ -164,6 +164,24 @@ def test_higher_order_kernels_match_oracle(types, kernel, prec):
     ref = oracle.solve(f, oracle.Problem(bc=bc, h=h, center=CELL, kernel=kernel))
     out, _ = cuda_solve(f, bc, CELL, prec, kernel)
     assert rel_linf(out, ref) < TOL[prec], rel_linf(out, ref)
+
+
+@pytest.mark.parametrize("types", [("UNB", "UNB", "UNB"), ("EU", "UNB", "UO"), ("UNB", "OU", "UE")],
+                         ids=["unb", "eu-unb-uo", "unb-ou-ue"])
+@pytest.mark.parametrize("prec", [F.F64, F.F32, F.F64E], ids=["f64", "f32", "f64e"])
+def test_lattice_green_matches_oracle(types, prec):
+    """LGF2 with every direction unbounded or semi-unbounded; cell-centred with unequal spacings
+    (16, 12 and 8 cells on the unit cube; power-of-two sizes for the double-float path)."""
+    shape = (8, 12, 16) if prec != F.F64E else (16, 16, 16)
+    rng = np.random.default_rng(47)
+    f = rng.standard_normal(shape)
+    n = (shape[2], shape[1], shape[0])
+    h = tuple(1.0 / n[d] for d in range(3))
+    bc = tuple(TYPES[t] for t in types)
+    ref = oracle.solve(f, oracle.Problem(bc=bc, h=h, center=CELL, kernel="lgf2"))
+    out, _ = cuda_solve(f, bc, CELL, prec, "lgf2")
+    tol = 1e-12 if prec == F.F64E else TOL[prec]
+    assert rel_linf(out, ref) < tol, rel_linf(out, ref)
 
 
 @pytest.mark.parametrize("kernel", ["hej4", "hej8"])
