@@ -108,10 +108,16 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   const bool cell = p.center == C_CELL;
   const int W2 = 2 * W, nm = p.n_modes;
   const bool rowmode = p.axis == 0;
-  const int tot = rowmode ? (W2 << p.ndlog) : nm * W2;
+  // compile-time tile in row mode: modes k < P/2 as 2W rows of P/2 (16 per thread, k fastest),
+  // then k = P/2 (every type has at most P/2 + 1 modes) on threads tid < 2W
+  const int tot = (PC > 0 && rowmode) ? W2 * (P / 2) + nthr : (rowmode ? (W2 << p.ndlog) : nm * W2);
   for (int idx = tid; idx < tot; idx += nthr) {
     int c, k;
-    if (rowmode) { k = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (k >= nm) continue; }
+    if (PC > 0 && rowmode) {
+      if (idx < W2 * (P / 2)) { c = idx / (P / 2); k = idx % (P / 2); }
+      else { c = idx - W2 * (P / 2); k = P / 2; if (c >= W2) continue; }
+      if (k >= nm) continue;
+    } else if (rowmode) { k = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (k >= nm) continue; }
     else { c = idx & (W2 - 1); k = idx / W2; }
     const int q = q0 + c;
     if (q >= p.npen) continue;
@@ -146,8 +152,36 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   const int ctype = comp_type(p, blockIdx.z);
   const int half = P / 2;
   const bool rowmode = p.axis == 0;
+  // (not on the double-float path, whose registers do not hold 18 modes per thread)
+  constexpr bool BATCH = PC > 0 && !std::is_same<T, dfloat>::value;
+  if (BATCH && rowmode) {
+    // compile-time tile in row mode: the W x P/2 modes k < P/2 are exactly 8 per thread
+    // (NT = P W / 16), all loads of a thread in flight together; lane = idx / (P/2) keeps
+    // k fastest (coalesced); the Nyquist modes k = P/2 go to threads tid < W in the same batch
+    constexpr int HP = PC / 2, NB8 = 8;
+    cpx<T> Xa[NB8 + 1], Xb[NB8 + 1];
+#pragma unroll
+    for (int u = 0; u <= NB8; ++u) {
+      const int idx = tid + u * nthr;
+      const int lane = u < NB8 ? idx / HP : tid, k = u < NB8 ? idx % HP : HP;
+      const int qa = q0 + 2 * lane, qb = qa + 1;
+      Xa[u] = mk<T>((T)0, (T)0);
+      Xb[u] = Xa[u];
+      if (u == NB8 && tid >= W) continue;
+      if (qa < p.npen) Xa[u] = stored_mode<T>(p, ctype, p.in, obase_i + (long long)qa * p.ai.ls, k, P, tw);
+      if (qb < p.npen) Xb[u] = stored_mode<T>(p, ctype, p.in, obase_i + (long long)qb * p.ai.ls, k, P, tw);
+    }
+#pragma unroll
+    for (int u = 0; u <= NB8; ++u) {
+      if (u == NB8 && tid >= W) continue;
+      const int idx = tid + u * nthr;
+      const int lane = u < NB8 ? idx / HP : tid, k = u < NB8 ? idx % HP : HP;
+      S[k * LS + lane] = mk<T>(Xa[u].x - Xb[u].y, Xa[u].y + Xb[u].x);
+      if (k != 0 && 2 * k != P) S[(P - k) * LS + lane] = mk<T>(Xa[u].x + Xb[u].y, Xb[u].x - Xa[u].y);
+    }
+  }
   // row mode: k fastest over a power-of-two stride (1 << p.hlog) >= half + 1
-  const int tot = rowmode ? (W << p.hlog) : (half + 1) * W;
+  const int tot = (BATCH && rowmode) ? 0 : (rowmode ? (W << p.hlog) : (half + 1) * W);
   constexpr int LOADB = 4;
   for (int base = tid; base < tot; base += LOADB * nthr) {
     cpx<T> Xa[LOADB], Xb[LOADB];
