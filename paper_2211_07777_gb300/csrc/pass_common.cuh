@@ -137,8 +137,13 @@ __device__ __forceinline__ void load_real_ext(const PassParams& p, int type, con
   T* Sr = reinterpret_cast<T*>(S);
   const int W2 = 2 * W;
   const bool rowmode = p.axis == 0;
-  // row mode: index i fastest over a power-of-two stride (1 << ndlog) >= nd
-  const int tot = rowmode ? (W2 << p.ndlog) : nd * W2;
+  // row mode: index i fastest.  Runtime tiles: over a power-of-two stride (1 << ndlog) >= nd.
+  // Compile-time tiles: rows of M = 2^floor(log2 nd) values, then the nd - M remaining ones
+  // (no idle iterations for node-centred counts such as 2^a + 1)
+  const int lgM = 31 - __clz(nd), M = 1 << lgM, rem = nd - M;
+  const bool exact = WC > 0 && rowmode;
+  const int tot_main = exact ? (W2 << lgM) : 0;
+  const int tot = exact ? tot_main + W2 * rem : (rowmode ? (W2 << p.ndlog) : nd * W2);
   // batches of LOADB independent loads per thread before their values are used (latency
   // hiding); the double-float path converts FP64 words on load and runs fastest unbatched
   constexpr int LOADB = std::is_same<T, dfloat>::value ? 1 : 8;
@@ -150,7 +155,10 @@ __device__ __forceinline__ void load_real_ext(const PassParams& p, int type, con
       const int idx = base + u * nthr;
       int c = 0, i = -1;
       if (idx < tot) {
-        if (rowmode) { i = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (i >= nd) i = -1; }
+        if (exact) {
+          if (idx < tot_main) { i = idx & (M - 1); c = idx >> lgM; }
+          else { const int r = idx - tot_main; c = r / rem; i = M + r % rem; }
+        } else if (rowmode) { i = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (i >= nd) i = -1; }
         else { c = idx & (W2 - 1); i = idx / W2; }
       }
       cc[u] = c;
@@ -179,10 +187,17 @@ __device__ __forceinline__ void store_real_data(const PassParams& p, int type, T
   const bool rev = is_reversed(type);
   const int W2 = 2 * W;
   const bool rowmode = p.axis == 0;
-  const int tot = rowmode ? (W2 << p.ndlog) : nd * W2;
+  // index spaces as in load_real_ext
+  const int lgM = 31 - __clz(nd), M = 1 << lgM, rem = nd - M;
+  const bool exact = WC > 0 && rowmode;
+  const int tot_main = exact ? (W2 << lgM) : 0;
+  const int tot = exact ? tot_main + W2 * rem : (rowmode ? (W2 << p.ndlog) : nd * W2);
   for (int idx = tid; idx < tot; idx += nthr) {
     int c, i;
-    if (rowmode) { i = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (i >= nd) continue; }
+    if (exact) {
+      if (idx < tot_main) { i = idx & (M - 1); c = idx >> lgM; }
+      else { const int r = idx - tot_main; c = r / rem; i = M + r % rem; }
+    } else if (rowmode) { i = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (i >= nd) continue; }
     else { c = idx & (W2 - 1); i = idx / W2; }
     const int q = q0 + c;
     if (q >= p.npen) continue;
