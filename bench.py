@@ -421,12 +421,31 @@ def run_served(args):
     pool = serve.HostPool()
     for r in reqs:
         pool.input(r)
-    warm = serve.run_stream(reqs[:64], budget, nstreams=args.streams, closed_loop=True, pool=pool)
-    cap = serve.run_stream(reqs, budget, nstreams=args.streams, closed_loop=True, pool=pool)
+    eng = args.fp64_engine
+    warm = serve.run_stream(reqs[:64], budget, nstreams=args.streams, closed_loop=True, pool=pool, fp64_engine=eng)
+    cap = serve.run_stream(reqs, budget, nstreams=args.streams, closed_loop=True, pool=pool, fp64_engine=eng)
     rate = 0.8 * cap["req_per_s"]
     nominal = 1.0 / np.mean(np.diff([r.arrival_s for r in reqs]))
     with ClockSampler(0) as clk:
-        run = serve.run_stream(reqs, budget, nstreams=args.streams, time_scale=nominal / rate, pool=pool)
+        run = serve.run_stream(reqs, budget, nstreams=args.streams, time_scale=nominal / rate, pool=pool,
+                               fp64_engine=eng)
+    n_df = sum(1 for r in reqs if serve.engine_prec(r, eng) == F.F64E)
+    # FP64-class requests on the double-float path: their error against the native FP64 path
+    df_errs = []
+    if n_df:
+        for r in [q for q in reqs if serve.engine_prec(q, eng) == F.F64E][:6]:
+            outs = []
+            for prec in (F.F64E, F.F64):
+                creq = serve.c_request(W.Request(**{**r.__dict__, "prec": F.F64}), "df" if prec == F.F64E else "native")
+                bc = [[tuple(creq.bc[(c * 3 + d) * 2:(c * 3 + d) * 2 + 2]) for d in range(3)] for c in range(3)]
+                sol = F.Solver(r.n, bc[0], prec=prec, op=r.op, green=r.kernel)
+                rhs = torch.from_numpy(np.ascontiguousarray(W.request_rhs(r))).to("cuda", torch.float64)
+                phi = torch.empty_like(rhs)
+                sol.solve(phi, rhs)
+                torch.cuda.synchronize()
+                outs.append(phi.cpu().numpy())
+                sol.close()
+            df_errs.append(float(np.abs(outs[0] - outs[1]).max() / np.abs(outs[1]).max()))
     # FP32 against FP64 on sampled request classes (same input), the stated error of the FP32 path
     errs = []
     for r in [q for q in reqs if q.prec == F.F32][:8]:
@@ -458,6 +477,8 @@ def run_served(args):
         "fp32": run.get("fp32"), "fp64": run.get("fp64"),
         "capacity_req_per_s": cap["req_per_s"], "capacity_mpts_per_s": cap["mpts_per_s"],
         "fp32_vs_fp64_max_rel_err": max(errs) if errs else None,
+        "fp64_engine": {"policy": eng, "requests_on_double_float": n_df,
+                        "double_float_vs_fp64_max_rel_err": max(df_errs) if df_errs else None},
         "server": run["server"], "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -551,6 +572,9 @@ def main():
     ap.add_argument("--no-variants", action="store_true", help="skip timing the other arithmetic paths")
     ap.add_argument("--served-requests", type=int, default=4096)
     ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--fp64-engine", default="native", choices=["native", "df"],
+                    help="served stream: FP64-class Poisson requests on power-of-two grids natively or on the "
+                         "double-float path (FP64 tolerance)")
     ap.add_argument("--profile", action="store_true",
                     help="only W warm-up and K solves, no checks or side measurements (for ncu captures)")
     args = ap.parse_args()

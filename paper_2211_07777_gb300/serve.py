@@ -33,9 +33,23 @@ def vector_bc(bc):
     return tuple(out)
 
 
-def c_request(req: W.Request):
+def _pow2(n):
+    return n >= 1 and (n & (n - 1)) == 0
+
+
+def engine_prec(req: W.Request, fp64_engine: str = "native") -> int:
+    """Arithmetic path for a request.  FP64-class requests run natively, or -- with
+    fp64_engine="df" -- on the double-float path (FP64 tolerance on the FP32 units) when it
+    applies: Poisson, every transform length a power of two (cell-centred N = 2^a)."""
+    if fp64_engine == "df" and req.prec == F.F64 and req.op == F.POISSON and all(_pow2(n) for n in req.n):
+        return F.F64E
+    return req.prec
+
+
+def c_request(req: W.Request, fp64_engine: str = "native"):
     bc = vector_bc(req.bc) if req.op == F.BIOT_SAVART else req.bc
-    return F.make_request(req.n, bc, center=F.CELL, prec=req.prec, op=req.op, green=req.kernel)
+    return F.make_request(req.n, bc, center=F.CELL, prec=engine_prec(req, fp64_engine), op=req.op,
+                          green=req.kernel)
 
 
 def _class_key(req):
@@ -69,11 +83,13 @@ class HostPool:
         self.free[_class_key(req)].append(buf)
 
 
-def run_stream(reqs, budget_bytes, nstreams=8, time_scale=1.0, closed_loop=False, keep=None, pool=None):
+def run_stream(reqs, budget_bytes, nstreams=8, time_scale=1.0, closed_loop=False, keep=None, pool=None,
+               fp64_engine="native"):
     """Submit reqs (sorted by arrival) and collect completions.
 
     time_scale multiplies the arrival times (open loop); closed_loop submits all at once.
     keep: set of request ids whose outputs are copied out and returned.
+    fp64_engine: "native" or "df" (see engine_prec).
     Returns a summary dict (+ 'outputs' for the kept ids)."""
     pool = pool or HostPool()
     for r in reqs:
@@ -108,7 +124,7 @@ def run_stream(reqs, budget_bytes, nstreams=8, time_scale=1.0, closed_loop=False
                         break
                     time.sleep(min(dt, 2e-4))
             out = pool.output(r)
-            tk = F.flups_server_submit(server, c_request(r), pool.input(r), out)
+            tk = F.flups_server_submit(server, c_request(r, fp64_engine), pool.input(r), out)
             inflight[tk] = (r, out)
             collect(F.flups_server_poll(server))
         while inflight:

@@ -61,6 +61,22 @@ def _need(req):
     return m["resident"] + m["transient"] + m["workspace"] + 2 * io
 
 
+def test_double_float_engine_in_the_mix_matches_native_fp64():
+    """With the df policy, FP64-class Poisson requests on power-of-two grids run on the
+    double-float path in the mix; each result stays within the FP64 tolerance of its native
+    FP64 solve alone."""
+    reqs = W.served_stream(nreq=16, seed=15, sizes=(32, 64))
+    assert any(serve.engine_prec(r, "df") == F.F64E for r in reqs)
+    out = serve.run_stream(reqs, 512 << 20, nstreams=4, closed_loop=True, keep={r.rid for r in reqs},
+                           fp64_engine="df")
+    assert out["completed"] == len(reqs) and out["errors"] == 0
+    for r in reqs:
+        ref = _alone(r)
+        got = out["outputs"][r.rid].numpy()
+        tol = 1e-12 if r.prec == F.F64 else 1e-5
+        assert np.abs(got - ref).max() <= tol * max(np.abs(ref).max(), 1e-300), r.rid
+
+
 def test_admission_by_memory_queues_evicts_and_refuses():
     import torch
     U, P = F.UNB, F.PER
