@@ -438,7 +438,7 @@ def run_served(args):
             for prec in (F.F64E, F.F64):
                 creq = serve.c_request(W.Request(**{**r.__dict__, "prec": F.F64}), "df" if prec == F.F64E else "native")
                 bc = [[tuple(creq.bc[(c * 3 + d) * 2:(c * 3 + d) * 2 + 2]) for d in range(3)] for c in range(3)]
-                sol = F.Solver(r.n, bc[0], prec=prec, op=r.op, green=r.kernel)
+                sol = F.Solver(r.n, bc if r.op == F.BIOT_SAVART else bc[0], prec=prec, op=r.op, green=r.kernel)
                 rhs = torch.from_numpy(np.ascontiguousarray(W.request_rhs(r))).to("cuda", torch.float64)
                 phi = torch.empty_like(rhs)
                 sol.solve(phi, rhs)
@@ -573,8 +573,7 @@ def main():
     ap.add_argument("--served-requests", type=int, default=4096)
     ap.add_argument("--streams", type=int, default=8)
     ap.add_argument("--fp64-engine", default="native", choices=["native", "df"],
-                    help="served stream: FP64-class Poisson requests on power-of-two grids natively or on the "
-                         "double-float path (FP64 tolerance)")
+                    help="served stream: FP64-class requests natively or on the double-float path (FP64 tolerance)")
     ap.add_argument("--profile", action="store_true",
                     help="only W warm-up and K solves, no checks or side measurements (for ncu captures)")
     args = ap.parse_args()

@@ -53,8 +53,8 @@ typedef enum { FLUPS_EVEN = 0, FLUPS_ODD = 1, FLUPS_PER = 3, FLUPS_UNB = 4 } flu
 typedef enum { FLUPS_CELL = 0, FLUPS_NODE = 1 } flups_center;
 /* Arithmetic of the transforms.  FLUPS_F64E: FP64 arrays (as FLUPS_F64) with
  * the transforms in double-float arithmetic on the FP32 units (about 48
- * significant bits, error within the FP64 path's 1e-12 bound); power-of-two
- * transform lengths (32..2048) and the Poisson operator only. */
+ * significant bits, error within the FP64 path's 1e-12 bound); every size,
+ * boundary condition, kernel and operator of the other paths. */
 typedef enum { FLUPS_F32 = 0, FLUPS_F64 = 1, FLUPS_F64E = 2 } flups_prec;
 /* Operator. */
 typedef enum { FLUPS_POISSON = 0, FLUPS_BIOT_SAVART = 1 } flups_op;

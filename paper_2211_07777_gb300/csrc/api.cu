@@ -298,6 +298,15 @@ int make_dsym(int P, double h, int diff, int prec, void** out, cudaStream_t st) 
     std::vector<float> f(v.begin(), v.end());
     CK(cudaMemcpyAsync(*out, f.data(), bytes, cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
+  } else if (prec == FLUPS_F64E) {
+    // double-float pairs (hi = nearest float, lo = nearest float of the remainder)
+    std::vector<float> f(2 * (size_t)P);
+    for (int kk = 0; kk < P; ++kk) {
+      f[2 * kk] = (float)v[kk];
+      f[2 * kk + 1] = (float)(v[kk] - (double)f[2 * kk]);
+    }
+    CK(cudaMemcpyAsync(*out, f.data(), bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
   } else {
     CK(cudaMemcpyAsync(*out, v.data(), bytes, cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
@@ -336,7 +345,7 @@ void fill_geom(Launch& L, const DirPlan& dp, int axis, const int* din, const int
   int wct = share == 1 ? ct_tile_width(dp.P, prec) : 0;  // the curl pass keeps the runtime engine
   const int other = axis == 0 ? 1 : (axis == 1 ? din[2] : din[1]);
   auto ctas = [&](int w) { return (long long)((p.npen + (packed ? 2 * w : w) - 1) / (packed ? 2 * w : w)) * other * ncomp; };
-  if (wct && prec != FLUPS_F64E && ctas(wct) < 2 * 152) wct = 0;  // small grid: narrower runtime tiles, more CTAs
+  if (wct && ctas(wct) < 2 * 152) wct = 0;  // small grid: narrower runtime tiles, more CTAs
   if (wct) {
     W = wct;
     nthr = dp.P * W / 16;
@@ -809,12 +818,6 @@ int flups_init_solver(flups_topo t, const int* bc, const double h[3], const doub
     }
   }
   if (rc == FLUPS_OK) rc = build_plan(s);
-  if (rc == FLUPS_OK && t->prec == FLUPS_F64E) {
-    // the double-float path is compiled for power-of-two transform lengths only, scalar operators
-    if (op == FLUPS_BIOT_SAVART) rc = FLUPS_EINVAL;
-    for (int d = 0; d < 3 && rc == FLUPS_OK; ++d)
-      if (ct_tile_width(s->dir[d].P, FLUPS_F64E) == 0) rc = FLUPS_ESIZE;
-  }
   if (rc == FLUPS_OK) {
     int du = 0;
     for (int d = 0; d < 3; ++d) du += s->dir[d].unb;

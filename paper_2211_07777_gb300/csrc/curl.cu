@@ -14,12 +14,15 @@
 // fused direction the derivative acts on the extension's DFT directly.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "pass_common.cuh"
 
 namespace flups {
 
 template <typename T> struct CurlMaxThreads { static constexpr int value = 512; };
 template <> struct CurlMaxThreads<double> { static constexpr int value = 256; };
+template <> struct CurlMaxThreads<dfloat> { static constexpr int value = 256; };
 
 // Per-pencil data: Green access and the derivative factors of the two non-axis
 // directions for each source component: fac[d][c] (complex).
@@ -70,21 +73,24 @@ __device__ __forceinline__ void pencil_curl_setup(const PassParams& p, int q, in
 template <typename T>
 __device__ __forceinline__ T curl_green(const PassParams& p, const PencilCurl<T>& pc, int g3) {
   const FusedGreen& g = p.g;
-  if (g.stored) {
-    const long long st3 = p.axis == 0 ? 1 : (p.axis == 1 ? (long long)g.gext[0] : (long long)g.gext[0] * g.gext[1]);
-    return __ldg(&((const T*)g.stored)[pc.goff + g3 * st3]);
+  if constexpr (!std::is_same<T, dfloat>::value) {
+    if (!g.stored) {
+      const T k2 = pc.k2p + ((const T*)g.tab[p.axis])[g3];
+      if (!(k2 > (T)0)) return (T)0;
+      if (g.kernel == 0 || g.kernel == 100) return -(T)g.scale / k2;
+      const int m = g.kernel / 2;
+      const T s = k2 * (T)g.eps2_half;
+      T acc = (T)1, term = (T)1;
+      for (int j = 1; j < m; ++j) {
+        term = term * s / (T)j;
+        acc += term;
+      }
+      return -(T)g.scale * exp(-s) * acc / k2;
+    }
   }
-  const T k2 = pc.k2p + ((const T*)g.tab[p.axis])[g3];
-  if (!(k2 > (T)0)) return (T)0;
-  if (g.kernel == 0 || g.kernel == 100) return -(T)g.scale / k2;
-  const int m = g.kernel / 2;
-  const T s = k2 * (T)g.eps2_half;
-  T acc = (T)1, term = (T)1;
-  for (int j = 1; j < m; ++j) {
-    term = term * s / (T)j;
-    acc += term;
-  }
-  return -(T)g.scale * exp(-s) * acc / k2;
+  // stored spectrum (always, on the double-float path)
+  const long long st3 = p.axis == 0 ? 1 : (p.axis == 1 ? (long long)g.gext[0] : (long long)g.gext[0] * g.gext[1]);
+  return ldg_r<T>(&((const T*)g.stored)[pc.goff + g3 * st3]);
 }
 
 // u_c = G (D_a f_b - D_b f_a), (a, b) = (c + 1, c + 2): F holds f^ of the pencil at one mode.
@@ -212,14 +218,18 @@ static cudaError_t set_curl_limits_t() {
 
 cudaError_t set_curl_smem_limits() {
   cudaError_t e = set_curl_limits_t<float>();
-  if (e) return e;
-  return set_curl_limits_t<double>();
+  if (!e) e = set_curl_limits_t<double>();
+  if (!e) e = set_curl_limits_t<dfloat>();
+  return e;
 }
 
 cudaError_t launch_curl(int kind, int prec, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st) {
   if (prec == 0) {
     if (kind == K_CURL_REAL) k_curl_real<float><<<grid, nthr, smem, st>>>(p);
     else k_curl_c2c<float><<<grid, nthr, smem, st>>>(p);
+  } else if (prec == 2) {
+    if (kind == K_CURL_REAL) k_curl_real<dfloat><<<grid, nthr, smem, st>>>(p);
+    else k_curl_c2c<dfloat><<<grid, nthr, smem, st>>>(p);
   } else {
     if (kind == K_CURL_REAL) k_curl_real<double><<<grid, nthr, smem, st>>>(p);
     else k_curl_c2c<double><<<grid, nthr, smem, st>>>(p);

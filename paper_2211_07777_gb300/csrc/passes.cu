@@ -1,4 +1,4 @@
-// Runtime-shaped pass kernels (any P = 2^a 3^b) and the launch dispatch.
+// Runtime-shaped pass kernels (any P = 2^a 3^b; FP32, FP64 and double-float) and the launch dispatch.
 #include <cuda_runtime.h>
 
 #include "pass_kernels.cuh"
@@ -22,6 +22,7 @@ int ct_tile_width(int P, int prec) {
 cudaError_t set_pass_smem_limits() {
   cudaError_t e = set_limits_kind<float, 0, 0>();
   if (!e) e = set_limits_kind<double, 0, 0>();
+  if (!e) e = set_limits_kind<dfloat, 0, 0>();
   if (!e) e = set_limits_ct_f32();
   if (!e) e = set_limits_ct_f64();
   if (!e) e = set_limits_ct_df();
@@ -29,7 +30,8 @@ cudaError_t set_pass_smem_limits() {
 }
 
 cudaError_t launch_pass(int kind, int prec, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st) {
-  if (prec == 2) return p.ct ? launch_ct_df(p.P, kind, p, grid, nthr, smem, st) : cudaErrorInvalidValue;
+  if (prec == 2) return p.ct ? launch_ct_df(p.P, kind, p, grid, nthr, smem, st)
+                             : launch_kind<dfloat, 0, 0>(kind, p, grid, nthr, smem, st);
   if (p.ct) return prec == 0 ? launch_ct_f32(p.P, kind, p, grid, nthr, smem, st)
                              : launch_ct_f64(p.P, kind, p, grid, nthr, smem, st);
   return prec == 0 ? launch_kind<float, 0, 0>(kind, p, grid, nthr, smem, st)

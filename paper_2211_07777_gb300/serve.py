@@ -33,15 +33,10 @@ def vector_bc(bc):
     return tuple(out)
 
 
-def _pow2(n):
-    return n >= 1 and (n & (n - 1)) == 0
-
-
 def engine_prec(req: W.Request, fp64_engine: str = "native") -> int:
     """Arithmetic path for a request.  FP64-class requests run natively, or -- with
-    fp64_engine="df" -- on the double-float path (FP64 tolerance on the FP32 units) when it
-    applies: Poisson, every transform length a power of two (cell-centred N = 2^a)."""
-    if fp64_engine == "df" and req.prec == F.F64 and req.op == F.POISSON and all(_pow2(n) for n in req.n):
+    fp64_engine="df" -- on the double-float path (FP64 tolerance on the FP32 units)."""
+    if fp64_engine == "df" and req.prec == F.F64:
         return F.F64E
     return req.prec
 

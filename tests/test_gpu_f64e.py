@@ -78,10 +78,36 @@ def test_double_float_unbounded_128_against_oracle():
     assert rel_linf(out, ref) < 1e-12
 
 
-def test_double_float_rejects_non_power_of_two_and_curl():
+def test_double_float_accepts_what_the_other_paths_accept():
+    """Sizes 2^a 3^b and the Biot-Savart operator build; sizes with other prime factors are
+    refused with FLUPS_ESIZE as on every path."""
+    F.Solver((24, 16, 16), ((PER, PER),) * 3, prec=F.F64E).close()
+    F.Solver((16, 16, 16), (((PER, PER),) * 3,) * 3, prec=F.F64E, op=F.BIOT_SAVART).close()
     with pytest.raises(F.FlupsError) as e:
-        F.Solver((24, 16, 16), ((PER, PER),) * 3, prec=F.F64E)
+        F.Solver((20, 16, 16), ((PER, PER),) * 3, prec=F.F64E)
     assert e.value.status == -3
-    with pytest.raises(F.FlupsError) as e:
-        F.Solver((16, 16, 16), (((PER, PER),) * 3,) * 3, prec=F.F64E, op=F.BIOT_SAVART)
-    assert e.value.status == -1
+
+
+@pytest.mark.parametrize("types", CASES[::3], ids=["-".join(c) for c in CASES[::3]])
+def test_double_float_transform_lengths_2a3b(types):
+    """Lengths 2^a 3^b (here 12 cells: 12, 24 or 48 per transform) run on the runtime-shaped
+    double-float tiles; small grids take them too."""
+    shape = (8, 12, 16)
+    rng = np.random.default_rng(zlib.crc32("-".join(types).encode()) % 1000 + 9)
+    f = rng.standard_normal(shape)
+    n = (shape[2], shape[1], shape[0])
+    h = tuple(1.0 / n[d] for d in range(3))
+    bc = tuple(TYPES[t] for t in types)
+    ref = oracle.solve(f, oracle.Problem(bc=bc, h=h, center=CELL, kernel=_kernel(types)))
+    out, _ = cuda_solve(f, bc, CELL, F.F64E, _kernel(types))
+    assert rel_linf(out, ref) < 1e-12, rel_linf(out, ref)
+
+
+def test_double_float_large_2a3b_against_fp64():
+    """96 x 192 x 64 cells (P up to 384): the double-float path against the native FP64 path."""
+    rng = np.random.default_rng(21)
+    f = rng.standard_normal((64, 192, 96))
+    bc = ((U, U), (PER, PER), (E, O))
+    a, _ = cuda_solve(f, bc, CELL, F.F64E, "hej2")
+    b, _ = cuda_solve(f, bc, CELL, F.F64, "hej2")
+    assert rel_linf(a, b) < 1e-12, rel_linf(a, b)
