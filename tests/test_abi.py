@@ -75,6 +75,17 @@ def test_host_validation(lib):
     assert e.value.status == -1
     _solver(F, (16, 16, 16), ((U, U), (U, U), (U, U)), green="hej0")
     _solver(F, (33, 33, 33), ((E, E), (O, E), (P, P)), center=1, green="lgf2")
+    _solver(F, (4, 4, 4), ((P, P), (U, U), (E, O)), green="hej2")      # the smallest grid: N = 4
+    _solver(F, (2048, 4, 4), ((U, U), (P, P), (P, P)), green="hej2")   # the longest transform: 2N = 4096
+    _solver(F, (1024, 4, 4), ((U, E), (P, P), (P, P)), green="hej2")   # semi-unbounded: 4N = 4096
+
+
+@pytest.mark.parametrize("n", [(0, 16, 16), (16, 0, 16), (-8, 16, 16), (2, 16, 16), (3, 16, 16)])
+def test_empty_negative_and_too_small_grids_are_refused(lib, n):
+    F = lib
+    with pytest.raises(F.FlupsError) as e:
+        _solver(F, n, ((F.PER, F.PER),) * 3)
+    assert e.value.status in (-1, -3)
 
 
 def test_solve_before_setup_is_a_state_error(lib):
