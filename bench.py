@@ -182,16 +182,21 @@ def traffic_record(kernel_name, workload_name):
     return rec.get("dram_bytes_per_launch")
 
 
+# the sources that define the compile-time pass kernels (the FFT engine, the tile loaders, the
+# pass kernels and their instantiations); the host planner and the other kernels are not among them
+KERNEL_SOURCES = ("fft_engine.cuh", "dfloat.cuh", "passes.cuh", "pass_common.cuh", "pass_kernels.cuh",
+                  "passes_ct_f32.cu", "passes_ct_f64.cu", "passes_ct_df.cu", "passes_ct_df_large.cu")
+
+
 def kernel_source_sha():
-    """Digest of every CUDA source and header of the library: a recorded ncu figure is used only
-    while the code it was taken on is unchanged."""
+    """Digest of the pass kernels' sources: a recorded ncu figure is used only while the kernel
+    code it was taken on is unchanged."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2211_07777_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, fn), "rb") as fh:
-                h.update(fn.encode())
-                h.update(fh.read())
+    for fn in KERNEL_SOURCES:
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fn.encode())
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
