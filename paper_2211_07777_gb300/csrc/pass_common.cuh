@@ -137,13 +137,46 @@ __device__ __forceinline__ void load_real_ext(const PassParams& p, int type, con
   T* Sr = reinterpret_cast<T*>(S);
   const int W2 = 2 * W;
   const bool rowmode = p.axis == 0;
-  // row mode: index i fastest.  Runtime tiles: over a power-of-two stride (1 << ndlog) >= nd.
-  // Compile-time tiles: rows of M = 2^floor(log2 nd) values, then the nd - M remaining ones
-  // (no idle iterations for node-centred counts such as 2^a + 1)
   const int lgM = 31 - __clz(nd), M = 1 << lgM, rem = nd - M;
-  const bool exact = WC > 0 && rowmode;
-  const int tot_main = exact ? (W2 << lgM) : 0;
-  const int tot = exact ? tot_main + W2 * rem : (rowmode ? (W2 << p.ndlog) : nd * W2);
+  if (WC > 0 && rowmode) {
+    // compile-time tile in row mode: a thread takes position i of both pencils of a lane (two
+    // coalesced loads, rows q0 + 2 lane and q0 + 2 lane + 1) and writes each image as one complex
+    // (a, b) -- one 8-byte shared store instead of two 4-byte ones.  Index space: rows of
+    // M = 2^floor(log2 nd) values, then the nd - M remaining ones.
+    const int tot_main = W << lgM, tot = tot_main + W * rem;
+    constexpr int LB = std::is_same<T, dfloat>::value ? 1 : 4;
+    for (int base = tid; base < tot; base += LB * nthr) {
+      T va[LB], vb[LB];
+      int ll[LB], ii[LB];
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int idx = base + u * nthr;
+        int lane = 0, i = -1;
+        if (idx < tot) {
+          if (idx < tot_main) { i = idx & (M - 1); lane = idx >> lgM; }
+          else { const int r = idx - tot_main; lane = r / rem; i = M + r % rem; }
+        }
+        ll[u] = lane;
+        ii[u] = i;
+        const int qa = q0 + 2 * lane;
+        const long long off = (long long)qa * p.ai.ls + (long long)i * p.ai.js;
+        va[u] = (i >= 0 && qa < p.npen) ? ld_real<T>(in, off, p.in_f64) : (T)0;
+        vb[u] = (i >= 0 && qa + 1 < p.npen) ? ld_real<T>(in, off + p.ai.ls, p.in_f64) : (T)0;
+      }
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        if (ii[u] < 0) continue;
+        const int dix = rev ? nd - 1 - ii[u] : ii[u];
+        int pos[4], sg[4];
+        const int n = images(t, p.center, N, dix, pos, sg);
+        for (int k = 0; k < n; ++k)
+          S[pos[k] * LS + ll[u]] = sg[k] > 0 ? mk<T>(va[u], vb[u]) : mk<T>(-va[u], -vb[u]);
+      }
+    }
+    return;
+  }
+  // runtime tiles in row mode: index i fastest over a power-of-two stride (1 << ndlog) >= nd
+  const int tot = rowmode ? (W2 << p.ndlog) : nd * W2;
   // batches of LOADB independent loads per thread before their values are used (latency
   // hiding); the double-float path converts FP64 words on load and runs fastest unbatched
   constexpr int LOADB = std::is_same<T, dfloat>::value ? 1 : 8;
@@ -155,10 +188,7 @@ __device__ __forceinline__ void load_real_ext(const PassParams& p, int type, con
       const int idx = base + u * nthr;
       int c = 0, i = -1;
       if (idx < tot) {
-        if (exact) {
-          if (idx < tot_main) { i = idx & (M - 1); c = idx >> lgM; }
-          else { const int r = idx - tot_main; c = r / rem; i = M + r % rem; }
-        } else if (rowmode) { i = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (i >= nd) i = -1; }
+        if (rowmode) { i = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (i >= nd) i = -1; }
         else { c = idx & (W2 - 1); i = idx / W2; }
       }
       cc[u] = c;
@@ -187,17 +217,31 @@ __device__ __forceinline__ void store_real_data(const PassParams& p, int type, T
   const bool rev = is_reversed(type);
   const int W2 = 2 * W;
   const bool rowmode = p.axis == 0;
-  // index spaces as in load_real_ext
   const int lgM = 31 - __clz(nd), M = 1 << lgM, rem = nd - M;
-  const bool exact = WC > 0 && rowmode;
-  const int tot_main = exact ? (W2 << lgM) : 0;
-  const int tot = exact ? tot_main + W2 * rem : (rowmode ? (W2 << p.ndlog) : nd * W2);
+  if (WC > 0 && rowmode) {
+    // compile-time tile in row mode: a thread reads one complex (a, b) of a lane and writes
+    // position i of both pencils (index space as in load_real_ext)
+    const int tot_main = W << lgM, tot = tot_main + W * rem;
+    for (int idx = tid; idx < tot; idx += nthr) {
+      int lane, i;
+      if (idx < tot_main) { i = idx & (M - 1); lane = idx >> lgM; }
+      else { const int r = idx - tot_main; lane = r / rem; i = M + r % rem; }
+      const int qa = q0 + 2 * lane;
+      if (qa >= p.npen) continue;
+      const int ii = rev ? nd - 1 - i : i;
+      const int pos = primary_pos(t, p.center, N, ii);
+      cpx<T> z = mk<T>((T)0, (T)0);
+      if (pos >= 0) z = S[pos * LS + lane];
+      const long long off = (long long)qa * p.ao.ls + (long long)i * p.ao.js;
+      st_real<T>(out, off, z.x, p.out_f64);
+      if (qa + 1 < p.npen) st_real<T>(out, off + p.ao.ls, z.y, p.out_f64);
+    }
+    return;
+  }
+  const int tot = rowmode ? (W2 << p.ndlog) : nd * W2;
   for (int idx = tid; idx < tot; idx += nthr) {
     int c, i;
-    if (exact) {
-      if (idx < tot_main) { i = idx & (M - 1); c = idx >> lgM; }
-      else { const int r = idx - tot_main; c = r / rem; i = M + r % rem; }
-    } else if (rowmode) { i = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (i >= nd) continue; }
+    if (rowmode) { i = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (i >= nd) continue; }
     else { c = idx & (W2 - 1); i = idx / W2; }
     const int q = q0 + c;
     if (q >= p.npen) continue;

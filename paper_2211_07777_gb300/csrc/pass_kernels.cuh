@@ -108,23 +108,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   const bool cell = p.center == C_CELL;
   const int W2 = 2 * W, nm = p.n_modes;
   const bool rowmode = p.axis == 0;
-  // compile-time tile in row mode: modes k < P/2 as 2W rows of P/2 (16 per thread, k fastest),
-  // then k = P/2 (every type has at most P/2 + 1 modes) on threads tid < 2W
-  const int tot = (PC > 0 && rowmode) ? W2 * (P / 2) + nthr : (rowmode ? (W2 << p.ndlog) : nm * W2);
-  for (int idx = tid; idx < tot; idx += nthr) {
-    int c, k;
-    if (PC > 0 && rowmode) {
-      if (idx < W2 * (P / 2)) { c = idx / (P / 2); k = idx % (P / 2); }
-      else { c = idx - W2 * (P / 2); k = P / 2; if (c >= W2) continue; }
-      if (k >= nm) continue;
-    } else if (rowmode) { k = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (k >= nm) continue; }
-    else { c = idx & (W2 - 1); k = idx / W2; }
-    const int q = q0 + c;
-    if (q >= p.npen) continue;
-    const int lane = c >> 1, part = c & 1;
-    const int kk = quarter ? 2 * k + 1 : k;
-    const int km = kk == 0 ? 0 : P - kk;
-    const cpx<T> X = split<T>(S[kk * LS + lane], S[km * LS + lane], part);
+  auto store_mode = [&](int q, int k, int kk, const cpx<T>& X) {
     const long long off = (long long)q * p.ao.ls + (long long)k * p.ao.js;
     if (cplx_out) {
       ((cpx<T>*)p.out)[obase_o + off] = X;
@@ -135,6 +119,38 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
       if (quarter) v = v * T(0.5);
       ((T*)p.out)[obase_o + off] = v;
     }
+  };
+  if (PC > 0 && rowmode) {
+    // compile-time tile in row mode: a thread reads Z_k and Z_{P-k} of a lane once and stores the
+    // mode of both of its pencils; modes k < P/2 as W rows of P/2 (8 per thread, k fastest), then
+    // k = P/2 (every type has at most P/2 + 1 modes) on threads tid < W
+    const int tot = W * (P / 2) + nthr;
+    for (int idx = tid; idx < tot; idx += nthr) {
+      int lane, k;
+      if (idx < W * (P / 2)) { lane = idx / (P / 2); k = idx % (P / 2); }
+      else { lane = idx - W * (P / 2); k = P / 2; if (lane >= W) continue; }
+      if (k >= nm) continue;
+      const int qa = q0 + 2 * lane;
+      if (qa >= p.npen) continue;
+      const int kk = quarter ? 2 * k + 1 : k;
+      const int km = kk == 0 ? 0 : P - kk;
+      const cpx<T> zk = S[kk * LS + lane], zm = S[km * LS + lane];
+      store_mode(qa, k, kk, split<T>(zk, zm, 0));
+      if (qa + 1 < p.npen) store_mode(qa + 1, k, kk, split<T>(zk, zm, 1));
+    }
+    return;
+  }
+  const int tot = rowmode ? (W2 << p.ndlog) : nm * W2;
+  for (int idx = tid; idx < tot; idx += nthr) {
+    int c, k;
+    if (rowmode) { k = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (k >= nm) continue; }
+    else { c = idx & (W2 - 1); k = idx / W2; }
+    const int q = q0 + c;
+    if (q >= p.npen) continue;
+    const int lane = c >> 1, part = c & 1;
+    const int kk = quarter ? 2 * k + 1 : k;
+    const int km = kk == 0 ? 0 : P - kk;
+    store_mode(q, k, kk, split<T>(S[kk * LS + lane], S[km * LS + lane], part));
   }
 }
 
