@@ -172,28 +172,38 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   constexpr bool BATCH = PC > 0 && !std::is_same<T, dfloat>::value;
   if (BATCH && rowmode) {
     // compile-time tile in row mode: the W x P/2 modes k < P/2 are exactly 8 per thread
-    // (NT = P W / 16), all loads of a thread in flight together; lane = idx / (P/2) keeps
-    // k fastest (coalesced); the Nyquist modes k = P/2 go to threads tid < W in the same batch
-    constexpr int HP = PC / 2, NB8 = 8;
-    cpx<T> Xa[NB8 + 1], Xb[NB8 + 1];
+    // (NT = P W / 16), loaded in batches of IB per thread (both pencils' modes of a lane);
+    // lane = idx / (P/2) keeps k fastest (coalesced); the Nyquist modes k = P/2 go to threads
+    // tid < W with the last batch
+    constexpr int HP = PC / 2, NB8 = 8, IB = 4;
 #pragma unroll
-    for (int u = 0; u <= NB8; ++u) {
-      const int idx = tid + u * nthr;
-      const int lane = u < NB8 ? idx / HP : tid, k = u < NB8 ? idx % HP : HP;
-      const int qa = q0 + 2 * lane, qb = qa + 1;
-      Xa[u] = mk<T>((T)0, (T)0);
-      Xb[u] = Xa[u];
-      if (u == NB8 && tid >= W) continue;
-      if (qa < p.npen) Xa[u] = stored_mode<T>(p, ctype, p.in, obase_i + (long long)qa * p.ai.ls, k, P, tw);
-      if (qb < p.npen) Xb[u] = stored_mode<T>(p, ctype, p.in, obase_i + (long long)qb * p.ai.ls, k, P, tw);
-    }
+    for (int u0 = 0; u0 < NB8; u0 += IB) {
+      constexpr int NI = IB + 1;
+      cpx<T> Xa[NI], Xb[NI];
+      const bool last = u0 + IB == NB8;
 #pragma unroll
-    for (int u = 0; u <= NB8; ++u) {
-      if (u == NB8 && tid >= W) continue;
-      const int idx = tid + u * nthr;
-      const int lane = u < NB8 ? idx / HP : tid, k = u < NB8 ? idx % HP : HP;
-      S[k * LS + lane] = mk<T>(Xa[u].x - Xb[u].y, Xa[u].y + Xb[u].x);
-      if (k != 0 && 2 * k != P) S[(P - k) * LS + lane] = mk<T>(Xa[u].x + Xb[u].y, Xb[u].x - Xa[u].y);
+      for (int e = 0; e < NI; ++e) {
+        const int u = u0 + e;
+        const bool nyq = e == IB;
+        const int idx = tid + u * nthr;
+        const int lane = nyq ? tid : idx / HP, k = nyq ? HP : idx % HP;
+        const int qa = q0 + 2 * lane, qb = qa + 1;
+        Xa[e] = mk<T>((T)0, (T)0);
+        Xb[e] = Xa[e];
+        if (nyq && !(last && tid < W)) continue;
+        if (qa < p.npen) Xa[e] = stored_mode<T>(p, ctype, p.in, obase_i + (long long)qa * p.ai.ls, k, P, tw);
+        if (qb < p.npen) Xb[e] = stored_mode<T>(p, ctype, p.in, obase_i + (long long)qb * p.ai.ls, k, P, tw);
+      }
+#pragma unroll
+      for (int e = 0; e < NI; ++e) {
+        const int u = u0 + e;
+        const bool nyq = e == IB;
+        if (nyq && !(last && tid < W)) continue;
+        const int idx = tid + u * nthr;
+        const int lane = nyq ? tid : idx / HP, k = nyq ? HP : idx % HP;
+        S[k * LS + lane] = mk<T>(Xa[e].x - Xb[e].y, Xa[e].y + Xb[e].x);
+        if (k != 0 && 2 * k != P) S[(P - k) * LS + lane] = mk<T>(Xa[e].x + Xb[e].y, Xb[e].x - Xa[e].y);
+      }
     }
   }
   // row mode: k fastest over a power-of-two stride (1 << p.hlog) >= half + 1
