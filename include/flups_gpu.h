@@ -143,6 +143,10 @@ int flups_solve_events(flups_solver s, void* phi, const void* rhs, void* stream,
  * algorithmic bytes (arrays read and written once, Green spectrum read once)
  * and nominal flops (5 P log2 P per complex FFT of length P). */
 int flups_pass_info(flups_solver s, int i, int* kind, int* axis, int* fft_len, double* bytes, double* flops);
+/* How pass i runs (bit flags): 1 compile-time tile engine, 2 Green slice staged in shared memory
+ * ahead of the multiply, 4 that slice copied by TMA (tensor map + mbarrier), 8 doubled transform
+ * pruned to its nonzero half.  Introspection only; no counterpart in the paper. */
+int flups_pass_features(flups_solver s, int i, int* flags);
 
 /* Allocation-free fully periodic solve (the paper has no counterpart; this is
  * an integration convenience).  For callers that must not allocate device
@@ -229,6 +233,13 @@ int flups_server_destroy(flups_server sv);
 const char* flups_strerror(int status);
 /* Text of the last CUDA error seen by the library in this process (static storage). */
 const char* flups_last_cuda_error(void);
+
+/* Device-side status of the solver's kernels since the last call: *code = 0, or
+ * the nonzero code a kernel left when one of its bounded waits gave up (1: the
+ * TMA copy of the Green slice in the fused pass did not complete in time; the
+ * solve's result is then not valid).  Synchronises the device, resets the code.
+ * No counterpart in the paper (device-side failure reporting). */
+int flups_solver_check(flups_solver s, int* code);
 
 /* Test hook: evaluate the device FP64 special functions used by the Green's
  * function generation at n points (device arrays x, y, out): which = 0 E1(x),

@@ -7,6 +7,7 @@
 // periodic, unbounded); the first periodic/unbounded direction met on real
 // data is an R2C transform, later ones are C2C.  The last direction is fused:
 // forward transform, multiplication by G^ (eq. poisson), inverse transform.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -140,6 +141,9 @@ struct flups_solver_s {
   void* W1 = nullptr;
   void* W2 = nullptr;
   void* green_dev = nullptr;
+  int green_pitch = 0;          // x pitch (elements) of the stored spectrum
+  void* gmaps_dev = nullptr;    // TMA tensor maps of the stored spectrum (fused column pass)
+  int* errflag = nullptr;       // device word set by bounded waits that give up
   void* tabs[3] = {nullptr, nullptr, nullptr};
   void* stage = nullptr;  // device copy of the caller's host arrays (flups_solve_host)
   size_t user_bytes = 0;
@@ -430,13 +434,15 @@ int setup_green(flups_solver_s* s, cudaStream_t st) {
       CK(cudaMallocAsync(&g64, n * sizeof(double), st));
       const double* tabs[3] = {(const double*)s->tabs[0], (const double*)s->tabs[1], (const double*)s->tabs[2]};
       cudaError_t e = launch_green_spectral(g64, gext, tabs, s->green, 0.5 * s->eps * s->eps, 1.0 / Pprod, st);
-      if (!e) e = cudaMallocAsync(&s->green_dev, n * 8, st);
-      if (!e) e = launch_green_finalize(g64, s->green_dev, prec, n, 1.0, st);
+      s->green_pitch = (gext[0] + 1) & ~1;  // 16-byte rows (8-byte elements)
+      const size_t padded = (size_t)s->green_pitch * gext[1] * gext[2] * 8;
+      if (!e) e = cudaMallocAsync(&s->green_dev, padded, st);
+      if (!e) e = launch_green_finalize(g64, s->green_dev, prec, n, gext[0], s->green_pitch, 1.0, st);
       cudaFreeAsync(g64, st);
       cudaError_t e2 = cudaStreamSynchronize(st);
       if (e || e2) return cuda_fail(e ? e : e2, "green spectral");
       s->green_bytes = (double)n * 8;
-      s->ws_bytes += (size_t)n * 8;
+      s->ws_bytes += padded;
     }
     return FLUPS_OK;
   }
@@ -487,14 +493,18 @@ int setup_green(flups_solver_s* s, cudaStream_t st) {
   }
   const double scale = vol / Pprod;
   const size_t bytes = n * esize(prec);
-  e = cudaMallocAsync(&s->green_dev, bytes, st);
+  // x rows padded to 16 bytes (TMA tensor maps need 16-byte strides)
+  const int per16 = (int)(16 / esize(prec));
+  s->green_pitch = (q.gext[0] + per16 - 1) / per16 * per16;
+  const size_t padded = (size_t)s->green_pitch * q.gext[1] * q.gext[2] * esize(prec);
+  e = cudaMallocAsync(&s->green_dev, padded, st);
   if (e) { cudaFreeAsync(g64, st); return cuda_fail(e, "green alloc"); }
-  e = launch_green_finalize(g64, s->green_dev, prec, n, scale, st);
+  e = launch_green_finalize(g64, s->green_dev, prec, n, q.gext[0], s->green_pitch, scale, st);
   cudaFreeAsync(g64, st);
   cudaError_t e2 = cudaStreamSynchronize(st);
   if (e || e2) return cuda_fail(e ? e : e2, "green finalize");
   s->green_bytes = (double)bytes;
-  s->ws_bytes += bytes;
+  s->ws_bytes += padded;
   return FLUPS_OK;
 }
 
@@ -564,7 +574,66 @@ int build_plan(flups_solver_s* s) {
   return FLUPS_OK;
 }
 
-int build_passes(flups_solver_s* s) {
+// TMA tensor maps of the stored Green spectrum for the fused column pass: a 3D map (x, y, z) with
+// the x rows at the spectrum's 16-byte pitch; map 0 has boxes of W lanes x gbox rows along the
+// fused axis, map 1 boxes of W lanes x 1 row (the last folded mode P/2).  The encoder comes from
+// the driver through the runtime's entry-point query, so the library links no driver library.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// Encodes both maps into the solver's device buffer; false (and no maps) when TMA does not apply.
+bool green_tensor_maps(flups_solver_s* s, int axis, int W, int P, int prec, int* gbox, cudaStream_t st) {
+  EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc || !s->green_dev || axis == 0) return false;
+  const size_t es = esize(prec);
+  if ((W * es) % 16 != 0 || (s->green_pitch * es) % 16 != 0) return false;
+  const int rb = std::min(256, P / 2);
+  if ((P / 2) % rb != 0) return false;
+  cuuint64_t dims[3], strides[2];
+  for (int d = 0; d < 3; ++d) dims[d] = (cuuint64_t)s->dir[d].gext;
+  strides[0] = (cuuint64_t)s->green_pitch * es;
+  strides[1] = strides[0] * (cuuint64_t)s->dir[1].gext;
+  const CUtensorMapDataType dt = prec == FLUPS_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUtensorMap maps[2];
+  for (int m = 0; m < 2; ++m) {
+    const cuuint32_t rows = m == 0 ? (cuuint32_t)rb : 1u;
+    const cuuint32_t box[3] = {(cuuint32_t)W, axis == 1 ? rows : 1u, axis == 2 ? rows : 1u};
+    if (enc(&maps[m], dt, 3, s->green_dev, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  if (!s->gmaps_dev && cudaMalloc(&s->gmaps_dev, sizeof(maps)) != cudaSuccess) {
+    cudaGetLastError();
+    s->gmaps_dev = nullptr;
+    return false;
+  }
+  if (cudaMemcpyAsync(s->gmaps_dev, maps, sizeof(maps), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  *gbox = rb;
+  return true;
+}
+
+int build_passes(flups_solver_s* s, cudaStream_t st) {
   const int prec = s->topo.prec, center = s->topo.center, nc = s->topo.ncomp;
   const int* o = s->order;
   const size_t es = esize(prec);
@@ -645,15 +714,19 @@ int build_passes(flups_solver_s* s) {
       g.gext[d] = s->dir[d].gext;
       g.fold[d] = (s->dir[d].role == R_C2C) ? s->dir[d].P : 0;
     }
+    g.gpitch = s->green_dev ? s->green_pitch : s->dir[0].gext;
     if (!curl && !real && L.p.ct && o[2] != 0 && g.stored && dp.gext == dp.P / 2 + 1) {
       // register-chained fused column kernel: stage the tile's Green slice in shared memory
       // (cp.async at kernel start) when that keeps the kernel's CTAs per SM
       const size_t gbytes = (size_t)L.p.W * (dp.P / 2 + 1) * esize(prec);
       const int threads = L.nthr;
       const int minb = std::max(1, (prec == FLUPS_F32 ? 1024 : 512) / threads);
-      if ((L.smem + gbytes + 1024) * minb <= 228 * 1024) {
-        L.smem += gbytes;
+      if ((L.smem + gbytes + 128 + 1024) * minb <= 228 * 1024) {
+        L.smem += gbytes + 128;  // + alignment of the slice to 128 bytes
         L.p.gpre = 1;
+        // the slice by TMA when the lanes' x indices are contiguous in the spectrum (x not folded)
+        if (g.fold[0] == 0 && green_tensor_maps(s, o[2], L.p.W, dp.P, prec, &L.p.gbox, st))
+          L.p.gmap = s->gmaps_dev;
       }
     }
     g.kernel = s->green;
@@ -876,10 +949,15 @@ int flups_setup(flups_solver s, void* stream, size_t* workspace_bytes) {
       s->ws_bytes += wbytes[i];
     }
   }
+  if (!s->errflag) {
+    CK(cudaMallocAsync((void**)&s->errflag, sizeof(int), st));
+    CK(cudaMemsetAsync(s->errflag, 0, sizeof(int), st));
+  }
   int rc = setup_green(s, st);
   if (rc) return rc;
-  rc = build_passes(s);
+  rc = build_passes(s, st);
   if (rc) return rc;
+  for (Launch& L : s->passes) L.p.errflag = s->errflag;
   CK(cudaStreamSynchronize(st));
   s->user_bytes = (size_t)s->topo.n[0] * s->topo.n[1] * s->topo.n[2] * nc * es;
   s->ready = true;
@@ -1009,6 +1087,15 @@ int flups_pass_info(flups_solver s, int i, int* kind, int* axis, int* fft_len, d
   return FLUPS_OK;
 }
 
+int flups_pass_features(flups_solver s, int i, int* flags) {
+  if (!s || !flags) return FLUPS_EINVAL;
+  if (!s->ready) return FLUPS_ESTATE;
+  if (i < 0 || i >= (int)s->passes.size()) return FLUPS_EINVAL;
+  const PassParams& p = s->passes[i].p;
+  *flags = (p.ct ? 1 : 0) | (p.gpre ? 2 : 0) | (p.gmap ? 4 : 0) | (p.hz ? 8 : 0);
+  return FLUPS_OK;
+}
+
 int flups_solve_host(flups_solver s, void* phi_host, const void* rhs_host, void* stream) {
   if (!s || !phi_host || !rhs_host) return FLUPS_EINVAL;
   if (!s->ready || s->shared) return FLUPS_ESTATE;
@@ -1046,6 +1133,11 @@ static void release(flups_solver s, cudaStream_t st, bool async) {
   fr(s->W2);
   fr(s->green_dev);
   fr(s->stage);
+  fr(s->errflag);
+  if (s->gmaps_dev) {
+    cudaFree(s->gmaps_dev);
+    s->gmaps_dev = nullptr;
+  }
 }
 
 int flups_cleanup(flups_solver s) {
@@ -1059,6 +1151,16 @@ int flups_cleanup_async(flups_solver s, void* stream) {
   if (!s) return FLUPS_OK;
   release(s, (cudaStream_t)stream, true);
   delete s;
+  return FLUPS_OK;
+}
+
+int flups_solver_check(flups_solver s, int* code) {
+  if (!s || !code) return FLUPS_EINVAL;
+  *code = 0;
+  if (!s->errflag) return FLUPS_OK;
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(code, s->errflag, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(s->errflag, 0, sizeof(int)));
   return FLUPS_OK;
 }
 

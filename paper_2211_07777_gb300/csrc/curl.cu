@@ -49,7 +49,7 @@ __device__ __forceinline__ void pencil_curl_setup(const PassParams& p, int q, in
   else { crd[0] = q; crd[1] = o; crd[2] = 0; }
   long long off = 0;
   T k2 = (T)0;
-  const long long st[3] = {1, (long long)g.gext[0], (long long)g.gext[0] * g.gext[1]};
+  const long long st[3] = {1, (long long)g.gpitch, (long long)g.gpitch * g.gext[1]};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     if (d == p.axis) continue;
@@ -89,7 +89,7 @@ __device__ __forceinline__ T curl_green(const PassParams& p, const PencilCurl<T>
     }
   }
   // stored spectrum (always, on the double-float path)
-  const long long st3 = p.axis == 0 ? 1 : (p.axis == 1 ? (long long)g.gext[0] : (long long)g.gext[0] * g.gext[1]);
+  const long long st3 = p.axis == 0 ? 1 : (p.axis == 1 ? (long long)g.gpitch : (long long)g.gpitch * g.gext[1]);
   return ldg_r<T>(&((const T*)g.stored)[pc.goff + g3 * st3]);
 }
 

@@ -425,18 +425,21 @@ cudaError_t launch_lgf(double* g, const int* gext, const double* h, cudaStream_t
   return e;
 }
 
+// Path-precision copy of the FP64 samples, x rows of gx values laid out with pitch gp >= gx.
 template <typename T>
-__global__ void k_green_finalize(const double* __restrict__ g, T* __restrict__ out, long long n, double scale) {
+__global__ void k_green_finalize(const double* __restrict__ g, T* __restrict__ out, long long n, int gx, int gp,
+                                 double scale) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    out[i] = (T)(g[i] * scale);
+    out[(i / gx) * gp + i % gx] = (T)(g[i] * scale);
 }
 
 // double-float storage: hi = nearest float, lo = nearest float of the remainder
-__global__ void k_green_finalize_df(const double* __restrict__ g, float2* __restrict__ out, long long n, double scale) {
+__global__ void k_green_finalize_df(const double* __restrict__ g, float2* __restrict__ out, long long n, int gx, int gp,
+                                    double scale) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double v = g[i] * scale;
     const float h = __double2float_rn(v);
-    out[i] = make_float2(h, __double2float_rn(v - (double)h));
+    out[(i / gx) * gp + i % gx] = make_float2(h, __double2float_rn(v - (double)h));
   }
 }
 
@@ -479,12 +482,13 @@ cudaError_t launch_green_sample(double* g, const GreenSampleParams& q, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_green_finalize(const double* g, void* out, int prec, long long n, double scale, cudaStream_t st) {
+cudaError_t launch_green_finalize(const double* g, void* out, int prec, long long n, int gx, int gp, double scale,
+                                  cudaStream_t st) {
   long long blocks = (n + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
-  if (prec == 0) k_green_finalize<float><<<(unsigned)blocks, 256, 0, st>>>(g, (float*)out, n, scale);
-  else if (prec == 2) k_green_finalize_df<<<(unsigned)blocks, 256, 0, st>>>(g, (float2*)out, n, scale);
-  else k_green_finalize<double><<<(unsigned)blocks, 256, 0, st>>>(g, (double*)out, n, scale);
+  if (prec == 0) k_green_finalize<float><<<(unsigned)blocks, 256, 0, st>>>(g, (float*)out, n, gx, gp, scale);
+  else if (prec == 2) k_green_finalize_df<<<(unsigned)blocks, 256, 0, st>>>(g, (float2*)out, n, gx, gp, scale);
+  else k_green_finalize<double><<<(unsigned)blocks, 256, 0, st>>>(g, (double*)out, n, gx, gp, scale);
   return cudaGetLastError();
 }
 

@@ -26,7 +26,9 @@ cudaError_t launch_green_sample(double* g, const GreenSampleParams& q, cudaStrea
 cudaError_t launch_lgf(double* g, const int* gext, const double* h, cudaStream_t st);
 // n-point Gauss-Legendre nodes and weights on [-1, 1] (host).
 void host_gauss_legendre(int n, double* x, double* w);
-cudaError_t launch_green_finalize(const double* g, void* out, int prec, long long n, double scale, cudaStream_t st);
+// out[(i / gx) gp + i % gx] = g[i] scale in the path precision (x rows of gx values at pitch gp)
+cudaError_t launch_green_finalize(const double* g, void* out, int prec, long long n, int gx, int gp, double scale,
+                                  cudaStream_t st);
 cudaError_t launch_green_spectral(double* g, const int* gext, const double* const* tabs, int kernel, double eps2h,
                                   double scale, cudaStream_t st);
 cudaError_t launch_special_eval(int which, const double* x, const double* y, double* out, int n, double eps,

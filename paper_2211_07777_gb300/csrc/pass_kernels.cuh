@@ -329,7 +329,7 @@ __device__ __forceinline__ void pencil_green_base(const PassParams& p, int q, in
   else { c[0] = q; c[1] = o; c[2] = 0; }
   long long off = 0;
   T k2 = (T)0;
-  const long long st[3] = {1, (long long)g.gext[0], (long long)g.gext[0] * g.gext[1]};
+  const long long st[3] = {1, (long long)g.gpitch, (long long)g.gpitch * g.gext[1]};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     if (d == p.axis) continue;
@@ -352,7 +352,7 @@ __device__ __forceinline__ T green_at(const PassParams& p, long long goff, T k2p
     }
   }
   // stored spectrum (always, on the double-float path)
-  const long long st3 = p.axis == 0 ? 1 : (p.axis == 1 ? (long long)g.gext[0] : (long long)g.gext[0] * g.gext[1]);
+  const long long st3 = p.axis == 0 ? 1 : (p.axis == 1 ? (long long)g.gpitch : (long long)g.gpitch * g.gext[1]);
   return ldg_r<T>(&((const T*)g.stored)[goff + g3 * st3]);
 }
 
@@ -637,12 +637,33 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
   long long* goff = reinterpret_cast<long long*>(smraw + (size_t)P * (W + 1) * sizeof(cpx<T>));
   T* k2p = reinterpret_cast<T*>(goff + W);
-  // stored spectrum slice of this tile, W lanes x (P/2 + 1) folded modes (p.gpre)
-  T* Gs = reinterpret_cast<T*>(smraw + (size_t)P * (W + 1) * sizeof(cpx<T>) + (size_t)W * (sizeof(long long) + sizeof(T)));
+  // stored spectrum slice of this tile, W lanes x (P/2 + 1) folded modes (p.gpre), at a 128-byte
+  // aligned shared address (the host adds the slack)
+  unsigned char* graw = smraw + (size_t)P * (W + 1) * sizeof(cpx<T>) + (size_t)W * (sizeof(long long) + sizeof(T));
+  T* Gs = reinterpret_cast<T*>(graw + ((128u - (smem_u32(graw) & 127u)) & 127u));
   constexpr int GH = P / 2 + 1;
   const int tid = threadIdx.x;
   const int q0 = blockIdx.x * W;
-  if (p.gpre) {
+  // the slice by TMA (p.gmap): one thread issues the box loads, completion through an mbarrier in
+  // the goff slot (unused on this path)
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(goff);
+  if (p.gpre && p.gmap) {
+    if (tid == 0) {
+      const FusedGreen& g = p.g;
+      const int nd = p.axis == 2 ? 1 : 2;  // the direction blockIdx.y runs along
+      const int o = blockIdx.y;
+      const int go = g.fold[nd] ? min(o, g.fold[nd] - o) : o;
+      const char* maps = (const char*)p.gmap;
+      mbar_init(mbar, 1);
+      mbar_expect_tx(mbar, (unsigned)(GH * W * sizeof(T)));
+      for (int r0 = 0; r0 < P / 2; r0 += p.gbox) {
+        if (p.axis == 2) tma_load_3d(Gs + (size_t)r0 * W, maps, q0, go, r0, mbar);
+        else tma_load_3d(Gs + (size_t)r0 * W, maps, q0, r0, go, mbar);
+      }
+      if (p.axis == 2) tma_load_3d(Gs + (size_t)(P / 2) * W, maps + 128, q0, go, P / 2, mbar);
+      else tma_load_3d(Gs + (size_t)(P / 2) * W, maps + 128, q0, P / 2, go, mbar);
+    }
+  } else if (p.gpre) {
     // asynchronous copy (cp.async) of the Green slice, overlapped with the forward transform;
     // NT is a multiple of W, so each thread serves one lane
     const int lane = tid % W;
@@ -650,7 +671,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     T kp;
     pencil_green_base<T>(p, q0 + lane, blockIdx.y, &go, &kp);
     if (q0 + lane < p.npen) {
-      const long long st3 = p.axis == 1 ? (long long)p.g.gext[0] : (long long)p.g.gext[0] * p.g.gext[1];
+      const long long st3 = p.axis == 1 ? (long long)p.g.gpitch : (long long)p.g.gpitch * p.g.gext[1];
       const T* src = (const T*)p.g.stored + go;
       for (int g3 = tid / W; g3 < GH; g3 += NT / W) cp_async_elem<sizeof(T)>(&Gs[g3 * W + lane], src + g3 * st3);
     }
@@ -668,8 +689,18 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   constexpr int RL = ct_rad(P, ct_nstages(P) - 1);
   constexpr int NB = 16 / RL;
   if (p.gpre) {
-    cp_async_wait_all();
-    __syncthreads();
+    if (p.gmap) {
+      // bounded wait for the TMA copies (mbarrier phase 0); a wait that gives up leaves code 1
+      bool done = false;
+      for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(mbar, 0);
+      if (!done) {
+        if (p.errflag) atomicExch(p.errflag, 1);
+        for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(mbar, 0);
+      }
+    } else {
+      cp_async_wait_all();
+      __syncthreads();
+    }
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int idx = tid + b * NT;

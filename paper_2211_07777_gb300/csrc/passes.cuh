@@ -35,6 +35,7 @@ struct FusedGreen {
   const void* stored;     // stored real spectrum (path precision) or nullptr for closed form
   const void* tab[3];     // closed form: per-direction |w|^2 (or FD symbol) tables, path precision
   int gext[3];            // Green index extents (x, y, z)
+  int gpitch;             // x pitch of the stored spectrum (elements): gext[0] rounded up to 16 bytes
   int fold[3];            // green index = fold ? min(i, fold - i) : i, for the two non-axis dirs
   int kernel;             // closed-form kernel id (0 spectral, 2..10 HEJ order, 100 LGF2)
   double eps2_half;       // eps^2 / 2
@@ -65,6 +66,10 @@ struct PassParams {
   int in_f64, out_f64;    // double-float path: the input / output is the caller's FP64 array
   int hz;                 // cell-centred doubled transform: half-zero input, half output kept (ct engine)
   int gpre;               // fused column pass: copy the tile's stored Green slice to shared memory up front
+  const void* gmap;       // with gpre: two TMA tensor maps of the stored spectrum (device memory, 128-byte
+                          // aligned; boxes of gbox rows and of 1 row along the fused axis), else nullptr
+  int gbox;               // rows per box of the first tensor map
+  int* errflag;           // device word: set to a nonzero code when a bounded wait gives up
   RadixPlan plan;
   const void* tw;         // exp(-2 pi i m/(2P)), m < 2P, path precision
   FusedGreen g;

@@ -29,7 +29,7 @@ EXPORTED = (
     "flups_debug_special", "flups_solve_pass", "flups_pass_info", "flups_solve_events", "flups_solve_periodic_noalloc",
     "flups_setup_shared", "flups_cleanup_async", "flups_workspace_size", "flups_solve_ws", "flups_solver_memory",
     "flups_server_create", "flups_server_submit", "flups_server_poll", "flups_server_wait", "flups_server_pending",
-    "flups_server_get_stats", "flups_server_destroy",
+    "flups_server_get_stats", "flups_server_destroy", "flups_solver_check", "flups_pass_features",
 )
 
 
@@ -89,6 +89,8 @@ def lib():
         L.flups_workspace_size.argtypes = [vp, szp]
         L.flups_solve_ws.argtypes = [vp, vp, vp, vp, vp]
         L.flups_solver_memory.argtypes = [vp, szp, szp, szp]
+        L.flups_solver_check.argtypes = [vp, ip]
+        L.flups_pass_features.argtypes = [vp, ctypes.c_int, ip]
         llp = ctypes.POINTER(ctypes.c_longlong)
         L.flups_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]
         L.flups_server_submit.argtypes = [vp, ctypes.POINTER(Request), vp, vp, llp]
@@ -356,6 +358,22 @@ class Solver:
 
     def solve_host(self, phi_host, rhs_host, stream=None):
         flups_solve_host(self._s, phi_host, rhs_host, stream)
+
+    def features(self):
+        """Per pass: dict(ct, staged_green, tma_green, pruned) (flups_pass_features)."""
+        out = []
+        for i in range(self.info["launches"]):
+            f = ctypes.c_int(0)
+            _check(lib().flups_pass_features(self._s, i, ctypes.byref(f)), "flups_pass_features")
+            v = f.value
+            out.append({"ct": bool(v & 1), "staged_green": bool(v & 2), "tma_green": bool(v & 4), "pruned": bool(v & 8)})
+        return out
+
+    def check(self) -> int:
+        """Device-side status since the last check (0, or the code of a bounded wait that gave up)."""
+        code = ctypes.c_int(0)
+        _check(lib().flups_solver_check(self._s, ctypes.byref(code)), "flups_solver_check")
+        return code.value
 
     def close(self):
         if getattr(self, "_s", None) is not None:
