@@ -136,6 +136,7 @@ struct flups_solver_s {
   DirPlan dir[3];
   int order[3];
   int dims[3][3];     // array dims after 0, 1, 2 forward passes
+  int pitch[3];       // x pitch of those arrays (the workspaces' rows padded to 16 bytes)
   int cplx[3];        // element type of those arrays (0 real, 1 complex)
   size_t elems1 = 0, elems2 = 0;
   void* W1 = nullptr;
@@ -247,13 +248,14 @@ void gauss_legendre(int n, double* x, double* w) {
 }
 
 
-ArrDesc arr_desc(const int* d, int axis) {
+// Strides of an array of d[0] x d[1] x d[2] values (x fastest) whose x rows are `pitch` apart.
+ArrDesc arr_desc(const int* d, int pitch, int axis) {
   ArrDesc a{};
-  const long long tot = (long long)d[0] * d[1] * d[2];
+  const long long tot = (long long)pitch * d[1] * d[2];
   a.cs = tot;
-  if (axis == 0) { a.ls = d[0]; a.js = 1; a.os = 0; }
-  else if (axis == 1) { a.ls = 1; a.js = d[0]; a.os = (long long)d[0] * d[1]; }
-  else { a.ls = 1; a.js = (long long)d[0] * d[1]; a.os = d[0]; }
+  if (axis == 0) { a.ls = pitch; a.js = 1; a.os = 0; }
+  else if (axis == 1) { a.ls = 1; a.js = pitch; a.os = (long long)pitch * d[1]; }
+  else { a.ls = 1; a.js = (long long)pitch * d[1]; a.os = pitch; }
   return a;
 }
 
@@ -339,10 +341,10 @@ void tile_shape(int P, int prec, int npen, bool packed, int* W, int* nthr, int s
 }
 
 void fill_geom(Launch& L, const DirPlan& dp, int axis, const int* din, const int* dout, int prec, bool packed,
-               int center, int ncomp, int share = 1) {
+               int center, int ncomp, int share = 1, int pin = -1, int pout = -1) {
   PassParams& p = L.p;
-  p.ai = arr_desc(din, axis);
-  p.ao = arr_desc(dout, axis);
+  p.ai = arr_desc(din, pin < 0 ? din[0] : pin, axis);
+  p.ao = arr_desc(dout, pout < 0 ? dout[0] : pout, axis);
   p.axis = axis;
   p.npen = axis == 0 ? din[1] * din[2] : din[0];
   int W, nthr;
@@ -571,7 +573,21 @@ int build_plan(flups_solver_s* s) {
     s->dims[i + 1][ord[i]] = dp.nm;
     s->cplx[i + 1] = s->cplx[i] || dp.role != R_R2R;
   }
+  // x pitch of each array: the caller's arrays are dense; the workspaces' rows are padded to
+  // 16 bytes so that TMA tensor maps can describe them
+  s->pitch[0] = s->dims[0][0];
+  for (int i = 1; i <= 2; ++i) {
+    const int elem = (s->cplx[i] ? 2 : 1) * (s->topo.prec == FLUPS_F32 ? 4 : 8);
+    const int per16 = elem >= 16 ? 1 : 16 / elem;
+    s->pitch[i] = (s->dims[i][0] + per16 - 1) / per16 * per16;
+  }
   return FLUPS_OK;
+}
+
+// Bytes of workspace array i (1: after d1, 2: after d2), padded rows, rounded to 256.
+size_t ws_array_bytes(const flups_solver_s* s, int i) {
+  return (((size_t)s->pitch[i] * s->dims[i][1] * s->dims[i][2] * s->topo.ncomp * (s->cplx[i] ? 2 : 1) *
+           (s->topo.prec == FLUPS_F32 ? 4 : 8)) + 255) & ~(size_t)255;
 }
 
 // TMA tensor maps of the stored Green spectrum for the fused column pass: a 3D map (x, y, z) with
@@ -653,7 +669,7 @@ int build_passes(flups_solver_s* s, cudaStream_t st) {
   {
     Launch L{};
     L.kind = K_FWD_REAL;
-    fill_geom(L, s->dir[o[0]], o[0], s->dims[0], s->dims[1], prec, true, center, nc);
+    fill_geom(L, s->dir[o[0]], o[0], s->dims[0], s->dims[1], prec, true, center, nc, 1, s->pitch[0], s->pitch[1]);
     L.p.ctypes = pack3(s->tf[0][o[0]], s->tf[1][o[0]], s->tf[2][o[0]]);
     L.p.out = s->W1;
     L.out_buf = 1;
@@ -669,7 +685,7 @@ int build_passes(flups_solver_s* s, cudaStream_t st) {
     Launch L{};
     const bool real = !s->cplx[1];
     L.kind = real ? K_FWD_REAL : K_FWD_C2C;
-    fill_geom(L, s->dir[o[1]], o[1], s->dims[1], s->dims[2], prec, real, center, nc);
+    fill_geom(L, s->dir[o[1]], o[1], s->dims[1], s->dims[2], prec, real, center, nc, 1, s->pitch[1], s->pitch[2]);
     L.p.ctypes = pack3(s->tf[0][o[1]], s->tf[1][o[1]], s->tf[2][o[1]]);
     L.p.in = s->W1;
     L.p.out = s->W2;
@@ -687,7 +703,8 @@ int build_passes(flups_solver_s* s, cudaStream_t st) {
     const bool curl = s->op == FLUPS_BIOT_SAVART;
     L.kind = curl ? (real ? K_CURL_REAL : K_CURL_C2C) : (real ? K_FUSED_REAL : K_FUSED_C2C);
     const DirPlan& dp = s->dir[o[2]];
-    fill_geom(L, dp, o[2], s->dims[2], s->dims[2], prec, real, center, curl ? 1 : nc, curl ? 3 : 1);
+    fill_geom(L, dp, o[2], s->dims[2], s->dims[2], prec, real, center, curl ? 1 : nc, curl ? 3 : 1, s->pitch[2],
+              s->pitch[2]);
     L.p.ctypes = pack3(s->tf[0][o[2]], s->tf[1][o[2]], s->tf[2][o[2]]);
     L.p.in = s->W2;
     L.p.out = s->W2;
@@ -745,7 +762,7 @@ int build_passes(flups_solver_s* s, cudaStream_t st) {
     Launch L{};
     const bool real = !s->cplx[1];
     L.kind = real ? K_INV_REAL : K_INV_C2C;
-    fill_geom(L, s->dir[o[1]], o[1], s->dims[2], s->dims[1], prec, real, center, nc);
+    fill_geom(L, s->dir[o[1]], o[1], s->dims[2], s->dims[1], prec, real, center, nc, 1, s->pitch[2], s->pitch[1]);
     L.p.ctypes = pack3(s->tu[0][o[1]], s->tu[1][o[1]], s->tu[2][o[1]]);
     L.p.in = s->W2;
     L.p.out = s->W1;
@@ -760,7 +777,7 @@ int build_passes(flups_solver_s* s, cudaStream_t st) {
   {
     Launch L{};
     L.kind = K_INV_REAL;
-    fill_geom(L, s->dir[o[0]], o[0], s->dims[1], s->dims[0], prec, true, center, nc);
+    fill_geom(L, s->dir[o[0]], o[0], s->dims[1], s->dims[0], prec, true, center, nc, 1, s->pitch[1], s->pitch[0]);
     L.p.ctypes = pack3(s->tu[0][o[0]], s->tu[1][o[0]], s->tu[2][o[0]]);
     L.p.in = s->W1;
     L.in_buf = 1;
@@ -933,9 +950,7 @@ int flups_setup(flups_solver s, void* stream, size_t* workspace_bytes) {
     s->ws_bytes += (size_t)4 * s->dir[d].P * es;
   }
   size_t wbytes[3] = {0, 0, 0};
-  for (int i = 1; i <= 2; ++i)
-    wbytes[i] = (((size_t)s->dims[i][0] * s->dims[i][1] * s->dims[i][2] * nc * (s->cplx[i] ? 2 : 1) * es) + 255) &
-                ~(size_t)255;
+  for (int i = 1; i <= 2; ++i) wbytes[i] = ws_array_bytes(s, i);
   s->ws_need = wbytes[1] + wbytes[2];
   if (!s->shared) {
     for (int i = 1; i <= 2; ++i) {
@@ -971,8 +986,7 @@ static int solve_impl(flups_solver s, void* phi, const void* rhs, void* ws, void
   const int prec = s->topo.prec;
   void* W[3] = {nullptr, s->W1, s->W2};
   if (ws) {
-    const size_t w1 = (((size_t)s->dims[1][0] * s->dims[1][1] * s->dims[1][2] * s->topo.ncomp * (s->cplx[1] ? 2 : 1) *
-                        esize(prec)) + 255) & ~(size_t)255;
+    const size_t w1 = ws_array_bytes(s, 1);
     W[1] = ws;
     W[2] = (char*)ws + w1;
   }
@@ -1016,8 +1030,7 @@ int flups_solver_memory(flups_solver s, size_t* resident, size_t* transient, siz
     res += gn * es;
     tr += gn * sizeof(double) + (size_t)8 * 2 * gmax * sizeof(double);
   }
-  for (int i = 1; i <= 2; ++i)
-    ws += (((size_t)s->dims[i][0] * s->dims[i][1] * s->dims[i][2] * nc * (s->cplx[i] ? 2 : 1) * es) + 255) & ~(size_t)255;
+  for (int i = 1; i <= 2; ++i) ws += ws_array_bytes(s, i);
   if (resident) *resident = res;
   if (transient) *transient = tr;
   if (workspace) *workspace = ws;
