@@ -390,6 +390,8 @@ void fill_geom(Launch& L, const DirPlan& dp, int axis, const int* din, const int
   L.grid = dim3((p.npen + per_tile - 1) / per_tile, axis == 0 ? 1 : (axis == 1 ? din[2] : din[1]), ncomp);
   L.nthr = nthr;
   L.smem = (p.ct ? 1 : 2) * (size_t)dp.P * p.LS * 2 * esize(prec) + 16 * 2 * W + 16;
+  // column kernels: 128-byte alignment of the tile and a 128-byte block for their mbarriers
+  if (p.ct && axis != 0 && (L.kind == K_FWD_C2C || L.kind == K_INV_C2C || L.kind == K_FUSED_C2C)) L.smem += 256;
 }
 
 int setup_green(flups_solver_s* s, cudaStream_t st) {
@@ -647,6 +649,45 @@ bool green_tensor_maps(flups_solver_s* s, int axis, int W, int P, int prec, int*
   }
   *gbox = rb;
   return true;
+}
+
+// TMA map of a column pass's input array (the T2 variant of a direction change: the tile arrives
+// by bulk tensor copies instead of per-thread loads).  4D: x in 8-byte units (one FP32 complex,
+// half an FP64 or double-float complex), y, z, component; the axis exposes the rows the pass reads
+// (n_use forward, P inverse; rows beyond arrive as zeros); boxes of W lanes x up to 256 rows.
+// Leaves p.tin_rows = 0 (per-thread loads) when the pass or the array does not qualify.
+void encode_input_map(Launch& L, int prec) {
+  PassParams& p = L.p;
+  p.tin_rows = 0;
+  const bool col = p.ct && p.axis != 0 && (L.kind == K_FWD_C2C || L.kind == K_INV_C2C || L.kind == K_FUSED_C2C);
+  EncodeTiledFn enc = tensor_map_encoder();
+  if (!col || !enc || !p.in) return;
+  const size_t cb = 2 * esize(prec);
+  const cuuint64_t u = cb / 8;
+  const bool inv = L.kind == K_INV_C2C;
+  const int n_in = inv ? p.P : p.n_use;
+  const int rows = (p.hz && !inv) ? p.P / 2 : p.P;
+  const int box = std::min(256, rows);
+  if (n_in > rows || rows % box != 0 || ((size_t)p.W * cb) % 16 != 0) return;
+  // measured: FP32 tiles gain at every length (unbounded 512^3: y inverse -15%, fused -4%); FP64 and
+  // double-float tiles gain with 128-byte rows (P <= 512) and lose with narrower ones (P = 1024:
+  // column passes +6..17%), where the per-thread loads overlap the first stage better
+  if (prec != FLUPS_F32 && (size_t)p.W * cb < 128) return;
+  const bool ax1 = p.axis == 1;
+  const cuuint64_t dims[4] = {(cuuint64_t)p.npen * u, (cuuint64_t)(ax1 ? n_in : (int)L.grid.y),
+                              (cuuint64_t)(ax1 ? (int)L.grid.y : n_in), (cuuint64_t)L.grid.z};
+  const cuuint64_t strides[3] = {(cuuint64_t)((ax1 ? p.ai.js : p.ai.os) * cb),
+                                 (cuuint64_t)((ax1 ? p.ai.os : p.ai.js) * cb), (cuuint64_t)(p.ai.cs * cb)};
+  for (int d = 0; d < 3; ++d)
+    if (strides[d] % 16 != 0) return;
+  const cuuint32_t boxd[4] = {(cuuint32_t)(p.W * u), ax1 ? (cuuint32_t)box : 1u, ax1 ? 1u : (cuuint32_t)box, 1u};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  if (enc(&p.tin, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, const_cast<void*>(p.in), dims, strides, boxd, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return;
+  p.tin_rows = rows;
+  p.tin_box = box;
 }
 
 int build_passes(flups_solver_s* s, cudaStream_t st) {
@@ -972,7 +1013,10 @@ int flups_setup(flups_solver s, void* stream, size_t* workspace_bytes) {
   if (rc) return rc;
   rc = build_passes(s, st);
   if (rc) return rc;
-  for (Launch& L : s->passes) L.p.errflag = s->errflag;
+  for (Launch& L : s->passes) {
+    L.p.errflag = s->errflag;
+    encode_input_map(L, prec);
+  }
   CK(cudaStreamSynchronize(st));
   s->user_bytes = (size_t)s->topo.n[0] * s->topo.n[1] * s->topo.n[2] * nc * es;
   s->ready = true;
@@ -991,11 +1035,13 @@ static int solve_impl(flups_solver s, void* phi, const void* rhs, void* ws, void
     W[2] = (char*)ws + w1;
   }
   for (Launch& L : s->passes) {
-    PassParams p = L.p;
+    Launch Lw = L;
+    PassParams& p = Lw.p;
     if (L.in_buf) p.in = W[L.in_buf];
     if (L.out_buf) p.out = W[L.out_buf];
     if (L.user_in) p.in = rhs;
     if (L.user_out) p.out = phi;
+    if (ws && L.in_buf) encode_input_map(Lw, prec);  // the caller's workspace: maps of its addresses
     cudaError_t e = L.kind >= K_CURL_REAL ? launch_curl(L.kind, prec, p, L.grid, L.nthr, L.smem, st)
                                           : launch_pass(L.kind, prec, p, L.grid, L.nthr, L.smem, st);
     if (e) return cuda_fail(e, "pass launch");

@@ -64,6 +64,25 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return ok != 0;
 }
+// 4D tile load of the box at coordinates (c0, c1, c2, c3) of the tensor map into shared memory
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0, int c1, int c2, int c3,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];\n" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+// Bounded wait for phase 0 of an mbarrier; a wait that gives up records `code` (and waits once
+// more, again bounded, for the copies in flight).
+__device__ __forceinline__ void mbar_wait_bounded(unsigned long long* bar, int* errflag, int code) {
+  bool done = false;
+  for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(bar, 0);
+  if (!done) {
+    if (errflag) atomicExch(errflag, code);
+    for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(bar, 0);
+  }
+}
 // 3D tile load of the box at coordinates (c0, c1, c2) of the tensor map into shared memory
 __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int c0, int c1, int c2,
                                             unsigned long long* bar) {

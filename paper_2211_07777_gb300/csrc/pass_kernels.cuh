@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
 // order so that its first butterflies read exactly those elements.  Shared
 // memory carries only the exchanges between stages.
 // ---------------------------------------------------------------------------
-enum XsMode : int { XS_SMEM = 0, XS_GLOBAL = 1, XS_REGS = 2 };
+enum XsMode : int { XS_SMEM = 0, XS_GLOBAL = 1, XS_REGS = 2, XS_NAT = 3 };  // XS_NAT: dense rows (TMA tile)
 
 template <typename T>
 struct ColIO {
@@ -522,6 +522,8 @@ __device__ __forceinline__ void xstage(cpx<T>* S, cpx<T>* v, const cpx<T>* __res
             const int hi = r * nbf;
             v[b * R + r] = S[((jx ^ CR::fold_c(hi >> LG)) + hi) * W + lane];
           }
+        } else if constexpr (SRC == XS_NAT) {
+          v[b * R + r] = S[i * W + lane];
         } else {
           const int q = io.q0 + lane;
           v[b * R + r] = (q < io.npen && i < io.n_in) ? io.in[(long long)q * io.ils + (long long)i * io.ijs]
@@ -529,7 +531,7 @@ __device__ __forceinline__ void xstage(cpx<T>* S, cpx<T>* v, const cpx<T>* __res
         }
       }
     }
-    if constexpr (SRC == XS_SMEM) __syncthreads();
+    if constexpr (SRC == XS_SMEM || SRC == XS_NAT) __syncthreads();
   }
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
@@ -611,59 +613,118 @@ __device__ __forceinline__ ColIO<T> col_io(const PassParams& p, int W, int n_in,
   return io;
 }
 
-template <typename T, int PC, int WC, bool HZ>
-__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fwd_c2c_col(PassParams p) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
-  cpx<T> v[16];
-  const ColIO<T> io = col_io<T>(p, WC, p.n_use, PC, -1);
-  xstages<T, PC, WC, false, false, 0, XS_GLOBAL, XS_GLOBAL, HZ, false>(S, v, (const cpx<T>*)p.tw, threadIdx.x, io);
+// Shared memory of the column kernels: the first 128-byte aligned address holds the input tile's
+// mbarrier; the tile S starts 128 bytes later (the host adds 256 bytes of slack).
+__device__ __forceinline__ unsigned char* col_base(unsigned char* smraw) {
+  return smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u) + 128;
+}
+
+// Input tile by TMA (p.tin_rows > 0): thread 0 initialises the mbarrier (all threads must pass a
+// barrier before waiting on it), then issues p.tin_rows / p.tin_box box loads of W lanes x tin_box
+// rows into the dense tile S (row i of lane l at S[i W + l]); rows past the array's extent arrive
+// as zeros.  p must be the kernel's __grid_constant__ parameter (the map is read in place).
+template <typename T, int W>
+__device__ __forceinline__ void tile_tma_issue(const PassParams& p, cpx<T>* S, unsigned long long* bar) {
+  constexpr int U = (int)sizeof(cpx<T>) / 8;  // 8-byte units per element
+  const int q0 = blockIdx.x * W, o = blockIdx.y, c = blockIdx.z;
+  mbar_expect_tx(bar, (unsigned)((size_t)p.tin_rows * W * sizeof(cpx<T>)));
+  for (int r0 = 0; r0 < p.tin_rows; r0 += p.tin_box) {
+    if (p.axis == 1) tma_load_4d(S + (size_t)r0 * W, &p.tin, q0 * U, r0, o, c, bar);
+    else tma_load_4d(S + (size_t)r0 * W, &p.tin, q0 * U, o, r0, c, bar);
+  }
 }
 
 template <typename T, int PC, int WC, bool HZ>
-__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_inv_c2c_col(PassParams p) {
+__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb)
+    k_fwd_c2c_col(const __grid_constant__ PassParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
+  unsigned char* base = col_base(smraw);
+  unsigned long long* mbar_in = reinterpret_cast<unsigned long long*>(base - 128);
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(base);
   cpx<T> v[16];
+  const int tid = threadIdx.x;
+  const ColIO<T> io = col_io<T>(p, WC, p.n_use, PC, -1);
+  const cpx<T>* tw = (const cpx<T>*)p.tw;
+  if (p.tin_rows) {
+    if (tid == 0) mbar_init(mbar_in, 1);
+    __syncthreads();
+    if (tid == 0) tile_tma_issue<T, WC>(p, S, mbar_in);
+    mbar_wait_bounded(mbar_in, p.errflag, 2);
+    xstages<T, PC, WC, false, false, 0, XS_NAT, XS_GLOBAL, HZ, false>(S, v, tw, tid, io);
+  } else {
+    xstages<T, PC, WC, false, false, 0, XS_GLOBAL, XS_GLOBAL, HZ, false>(S, v, tw, tid, io);
+  }
+}
+
+template <typename T, int PC, int WC, bool HZ>
+__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb)
+    k_inv_c2c_col(const __grid_constant__ PassParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  unsigned char* base = col_base(smraw);
+  unsigned long long* mbar_in = reinterpret_cast<unsigned long long*>(base - 128);
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(base);
+  cpx<T> v[16];
+  const int tid = threadIdx.x;
   const int dup = (p.type == T_PER && p.center == C_NODE && p.n_data > p.N) ? p.N : -1;
   const ColIO<T> io = col_io<T>(p, WC, PC, p.n_data, dup);
-  xstages<T, PC, WC, true, false, 0, XS_GLOBAL, XS_GLOBAL, false, HZ>(S, v, (const cpx<T>*)p.tw, threadIdx.x, io);
+  const cpx<T>* tw = (const cpx<T>*)p.tw;
+  if (p.tin_rows) {
+    if (tid == 0) mbar_init(mbar_in, 1);
+    __syncthreads();
+    if (tid == 0) tile_tma_issue<T, WC>(p, S, mbar_in);
+    mbar_wait_bounded(mbar_in, p.errflag, 2);
+    xstages<T, PC, WC, true, false, 0, XS_NAT, XS_GLOBAL, false, HZ>(S, v, tw, tid, io);
+  } else {
+    xstages<T, PC, WC, true, false, 0, XS_GLOBAL, XS_GLOBAL, false, HZ>(S, v, tw, tid, io);
+  }
 }
 
 template <typename T, int PC, int WC, bool HZ>
-__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fused_c2c_col(PassParams p) {
+__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb)
+    k_fused_c2c_col(const __grid_constant__ PassParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int P = PC, W = WC, NT = PC * WC / 16;
-  cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
-  long long* goff = reinterpret_cast<long long*>(smraw + (size_t)P * (W + 1) * sizeof(cpx<T>));
+  unsigned char* base = col_base(smraw);
+  unsigned long long* mbar_in = reinterpret_cast<unsigned long long*>(base - 128);
+  unsigned long long* mbar_g = mbar_in + 1;
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(base);
+  long long* goff = reinterpret_cast<long long*>(base + (size_t)P * (W + 1) * sizeof(cpx<T>));
   T* k2p = reinterpret_cast<T*>(goff + W);
   // stored spectrum slice of this tile, W lanes x (P/2 + 1) folded modes (p.gpre), at a 128-byte
   // aligned shared address (the host adds the slack)
-  unsigned char* graw = smraw + (size_t)P * (W + 1) * sizeof(cpx<T>) + (size_t)W * (sizeof(long long) + sizeof(T));
+  unsigned char* graw = base + (size_t)P * (W + 1) * sizeof(cpx<T>) + (size_t)W * (sizeof(long long) + sizeof(T));
   T* Gs = reinterpret_cast<T*>(graw + ((128u - (smem_u32(graw) & 127u)) & 127u));
   constexpr int GH = P / 2 + 1;
   const int tid = threadIdx.x;
   const int q0 = blockIdx.x * W;
-  // the slice by TMA (p.gmap): one thread issues the box loads, completion through an mbarrier in
-  // the goff slot (unused on this path)
-  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(goff);
-  if (p.gpre && p.gmap) {
+  const bool tma_g = p.gpre && p.gmap;
+  // TMA copies: the input tile (p.tin_rows) and the Green slice (p.gmap), each completed on its
+  // own mbarrier; thread 0 initialises both before the CTA barrier and then issues the loads
+  if (p.tin_rows || tma_g) {
     if (tid == 0) {
-      const FusedGreen& g = p.g;
-      const int nd = p.axis == 2 ? 1 : 2;  // the direction blockIdx.y runs along
-      const int o = blockIdx.y;
-      const int go = g.fold[nd] ? min(o, g.fold[nd] - o) : o;
-      const char* maps = (const char*)p.gmap;
-      mbar_init(mbar, 1);
-      mbar_expect_tx(mbar, (unsigned)(GH * W * sizeof(T)));
-      for (int r0 = 0; r0 < P / 2; r0 += p.gbox) {
-        if (p.axis == 2) tma_load_3d(Gs + (size_t)r0 * W, maps, q0, go, r0, mbar);
-        else tma_load_3d(Gs + (size_t)r0 * W, maps, q0, r0, go, mbar);
-      }
-      if (p.axis == 2) tma_load_3d(Gs + (size_t)(P / 2) * W, maps + 128, q0, go, P / 2, mbar);
-      else tma_load_3d(Gs + (size_t)(P / 2) * W, maps + 128, q0, P / 2, go, mbar);
+      if (p.tin_rows) mbar_init(mbar_in, 1);
+      if (tma_g) mbar_init(mbar_g, 1);
     }
-  } else if (p.gpre) {
+    __syncthreads();
+    if (tid == 0) {
+      if (p.tin_rows) tile_tma_issue<T, W>(p, S, mbar_in);
+      if (tma_g) {
+        const FusedGreen& g = p.g;
+        const int nd = p.axis == 2 ? 1 : 2;  // the direction blockIdx.y runs along
+        const int o = blockIdx.y;
+        const int go = g.fold[nd] ? min(o, g.fold[nd] - o) : o;
+        const char* maps = (const char*)p.gmap;
+        mbar_expect_tx(mbar_g, (unsigned)(GH * W * sizeof(T)));
+        for (int r0 = 0; r0 < P / 2; r0 += p.gbox) {
+          if (p.axis == 2) tma_load_3d(Gs + (size_t)r0 * W, maps, q0, go, r0, mbar_g);
+          else tma_load_3d(Gs + (size_t)r0 * W, maps, q0, r0, go, mbar_g);
+        }
+        if (p.axis == 2) tma_load_3d(Gs + (size_t)(P / 2) * W, maps + 128, q0, go, P / 2, mbar_g);
+        else tma_load_3d(Gs + (size_t)(P / 2) * W, maps + 128, q0, P / 2, go, mbar_g);
+      }
+    }
+  }
+  if (p.gpre && !tma_g) {
     // asynchronous copy (cp.async) of the Green slice, overlapped with the forward transform;
     // NT is a multiple of W, so each thread serves one lane
     const int lane = tid % W;
@@ -676,27 +737,26 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
       for (int g3 = tid / W; g3 < GH; g3 += NT / W) cp_async_elem<sizeof(T)>(&Gs[g3 * W + lane], src + g3 * st3);
     }
     cp_async_commit();
-  } else {
+  } else if (!p.gpre) {
     for (int lane = tid; lane < W; lane += NT) pencil_green_base<T>(p, q0 + lane, blockIdx.y, &goff[lane], &k2p[lane]);
   }
   const int dup = (p.type == T_PER && p.center == C_NODE && p.n_data > p.N) ? p.N : -1;
   const ColIO<T> io = col_io<T>(p, W, p.n_use, p.n_data, dup);
   const cpx<T>* tw = (const cpx<T>*)p.tw;
   cpx<T> v[16];
-  // forward: HBM -> ... -> registers (the first stage's barrier also publishes goff/k2p)
-  xstages<T, P, W, false, false, 0, XS_GLOBAL, XS_REGS, HZ, false>(S, v, tw, tid, io);
+  // forward: HBM (or the TMA tile) -> ... -> registers (the first stage's barrier also publishes goff/k2p)
+  if (p.tin_rows) {
+    mbar_wait_bounded(mbar_in, p.errflag, 2);
+    xstages<T, P, W, false, false, 0, XS_NAT, XS_REGS, HZ, false>(S, v, tw, tid, io);
+  } else {
+    xstages<T, P, W, false, false, 0, XS_GLOBAL, XS_REGS, HZ, false>(S, v, tw, tid, io);
+  }
   // u^ = G^ f^ on the 16 elements this thread holds: indices j + r P/RL
   constexpr int RL = ct_rad(P, ct_nstages(P) - 1);
   constexpr int NB = 16 / RL;
   if (p.gpre) {
-    if (p.gmap) {
-      // bounded wait for the TMA copies (mbarrier phase 0); a wait that gives up leaves code 1
-      bool done = false;
-      for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(mbar, 0);
-      if (!done) {
-        if (p.errflag) atomicExch(p.errflag, 1);
-        for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(mbar, 0);
-      }
+    if (tma_g) {
+      mbar_wait_bounded(mbar_g, p.errflag, 1);
     } else {
       cp_async_wait_all();
       __syncthreads();

@@ -1,5 +1,6 @@
 // Pass descriptors shared by the host planner and the pass kernels.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -70,6 +71,10 @@ struct PassParams {
                           // aligned; boxes of gbox rows and of 1 row along the fused axis), else nullptr
   int gbox;               // rows per box of the first tensor map
   int* errflag;           // device word: set to a nonzero code when a bounded wait gives up
+  // column passes of the compile-time engine: the input tile by TMA (0 rows: loads from registers)
+  int tin_rows;           // rows along the axis copied into the tile (P/2 when pruned, else P)
+  int tin_box;            // rows per TMA box
+  CUtensorMap tin;        // 4D map of the input array: (x in 8-byte units, y, z, component)
   RadixPlan plan;
   const void* tw;         // exp(-2 pi i m/(2P)), m < 2P, path precision
   FusedGreen g;
