@@ -404,6 +404,8 @@ def run_ours(args):
         else:
             line["cpu_baseline"] = {"value": None, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
                                     "sample": "skipped: the oracle's full extended box does not fit a bounded sample"}
+    # device-side status of every solve above (0: no bounded wait gave up; checked outside timing)
+    line["device_status"] = solver.check()
     if rank == 0:
         print(json.dumps(line), flush=True)
     solver.close()
