@@ -18,6 +18,8 @@ def cuda_solve(f, bc, center, prec, kernel, L=(1.0, 1.0, 1.0), eps_over_h=2.0, o
         phi = rhs if in_place else torch.empty_like(rhs)
         s.solve(phi, rhs)
         torch.cuda.synchronize()
+        code = s.check()
+        assert code == 0, f"a bounded device wait gave up (code {code})"
         return phi.double().cpu().numpy(), s.info
     finally:
         s.close()

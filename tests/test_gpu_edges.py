@@ -60,3 +60,19 @@ def test_constant_right_hand_side_periodic_is_the_zero_mode(prec):
     f = np.full((16, 16, 32), 3.0)
     out, _ = cuda_solve(f, ((PER, PER),) * 3, CELL, prec, "spectral")
     assert np.abs(out).max() < (1e-5 if prec == F.F32 else 1e-12)
+
+
+_LONG = {}
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=IDS)
+def test_longest_column_transform(prec):
+    """z unbounded with 1024 cells: the fused column pass runs the compile-time tile at P = 2048
+    (4 lanes FP32, 2 lanes FP64 and double-float), fed by TMA where that applies."""
+    shape = (1024, 64, 64)
+    bc = ((PER, PER), (PER, PER), (U, U))
+    if not _LONG:
+        _LONG["case"] = _case(shape, bc, CELL, "hej2", 63)
+    f, ref = _LONG["case"]
+    out, _ = cuda_solve(f, bc, CELL, prec, "hej2")
+    assert rel_linf(out, ref) < TOL[prec], rel_linf(out, ref)
