@@ -485,14 +485,18 @@ int setup_green(flups_solver_s* s, cudaStream_t st) {
     gp.P = 2 * gp.N;
     gp.nm = dp.gext;
     gp.rp = radix_plan(gp.P);
-    int rc = make_twiddles(gp.P, FLUPS_F64, &gp.tw);
+    // in double-float arithmetic on the FP32 units (FP64 samples in and out, ~1e-14 relative):
+    // GB300's FP64 units would make these passes the bulk of a plan's setup time
+    int rc = make_twiddles(gp.P, FLUPS_F64E, &gp.tw);
     if (rc) { cudaFreeAsync(g64, st); return rc; }
     Launch L{};
     L.kind = K_FWD_REAL;
-    fill_geom(L, gp, d, q.gext, q.gext, FLUPS_F64, true, FLUPS_NODE, 1);
+    fill_geom(L, gp, d, q.gext, q.gext, FLUPS_F64E, true, FLUPS_NODE, 1);
     L.p.in = g64;
     L.p.out = g64;
-    e = launch_pass(L.kind, FLUPS_F64, L.p, L.grid, L.nthr, L.smem, st);
+    L.p.in_f64 = 1;
+    L.p.out_f64 = 1;
+    e = launch_pass(L.kind, FLUPS_F64E, L.p, L.grid, L.nthr, L.smem, st);
     if (e) { cudaFreeAsync(g64, st); return cuda_fail(e, "green DCT-I"); }
   }
   const double scale = vol / Pprod;

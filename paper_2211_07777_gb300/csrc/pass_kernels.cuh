@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
       if (cell) F = cmul<T>(X, ldg_c<T>(&tw[kk]));
       T v = oddo ? -F.y : F.x;
       if (quarter) v = v * T(0.5);
-      ((T*)p.out)[obase_o + off] = v;
+      st_real<T>((T*)p.out, obase_o + off, v, p.out_f64);
     }
   };
   if (PC > 0 && rowmode) {
