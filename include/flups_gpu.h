@@ -234,6 +234,14 @@ const char* flups_strerror(int status);
 /* Text of the last CUDA error seen by the library in this process (static storage). */
 const char* flups_last_cuda_error(void);
 
+/* Opt in, before flups_setup, to sharing the stored Green spectrum with other
+ * solvers of the process that store the same data (same device, precision,
+ * kernel, eps and per-direction sampling).  The last sharing solver released
+ * frees it, stream-ordered on its release stream: release a sharing solver
+ * only when no solve of any solver sharing its spectrum is still in flight
+ * (the serving runtime releases idle plans only).  No counterpart in the paper. */
+int flups_solver_share_green(flups_solver s);
+
 /* Device-side status of the solver's kernels since the last call: *code = 0, or
  * the nonzero code a kernel left when one of its bounded waits gave up (1: the
  * TMA copy of the Green slice in the fused pass did not complete in time; the

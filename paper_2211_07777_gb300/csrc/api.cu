@@ -143,6 +143,8 @@ struct flups_solver_s {
   void* W2 = nullptr;
   void* green_dev = nullptr;
   int green_pitch = 0;          // x pitch (elements) of the stored spectrum
+  bool share_green = false;     // look the stored spectrum up in (and add it to) the process-wide cache
+  std::string green_key;        // its cache key when shared
   void* gmaps_dev = nullptr;    // TMA tensor maps of the stored spectrum (fused column pass)
   int* errflag = nullptr;       // device word set by bounded waits that give up
   void* tabs[3] = {nullptr, nullptr, nullptr};
@@ -394,7 +396,7 @@ void fill_geom(Launch& L, const DirPlan& dp, int axis, const int* din, const int
   if (p.ct && axis != 0 && (L.kind == K_FWD_C2C || L.kind == K_INV_C2C || L.kind == K_FUSED_C2C)) L.smem += 256;
 }
 
-int setup_green(flups_solver_s* s, cudaStream_t st) {
+int setup_green_compute(flups_solver_s* s, cudaStream_t st) {
   const int prec = s->topo.prec;
   int du = 0;
   for (int d = 0; d < 3; ++d) du += s->dir[d].unb;
@@ -513,6 +515,81 @@ int setup_green(flups_solver_s* s, cudaStream_t st) {
   if (e || e2) return cuda_fail(e ? e : e2, "green finalize");
   s->green_bytes = (double)bytes;
   s->ws_bytes += padded;
+  return FLUPS_OK;
+}
+
+// Stored spectra shared between solvers (the serving runtime): solvers whose spectra are the same
+// data -- same device, precision, kernel, eps and, per direction, the same sampling (unbounded-
+// like: gext, P, h) or wavenumbers (spectral: gext, P, wscale, wshift) -- hold one device copy.
+// Solvers opt in (flups_solver_share_green); the last one released frees it, stream-ordered on its
+// release stream, which is safe when no solve of any sharing solver is still in flight (the
+// serving runtime releases idle plans only).
+struct GreenEntry {
+  void* dev;
+  int pitch;
+  double bytes;
+  size_t padded;
+  int refs;
+};
+std::mutex g_green_mu;
+std::map<std::string, GreenEntry> g_green_cache;
+
+std::string green_cache_key(const flups_solver_s* s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::string k;
+  auto put = [&](const void* p, size_t n) { k.append((const char*)p, n); };
+  put(&dev, sizeof dev);
+  put(&s->topo.prec, sizeof s->topo.prec);
+  put(&s->green, sizeof s->green);
+  put(&s->eps, sizeof s->eps);
+  for (int d = 0; d < 3; ++d) {
+    const DirPlan& dp = s->dir[d];
+    put(&dp.unb, sizeof dp.unb);
+    put(&dp.gext, sizeof dp.gext);
+    put(&dp.P, sizeof dp.P);
+    put(&dp.h, sizeof dp.h);
+    if (!dp.unb) {
+      put(&dp.wscale, sizeof dp.wscale);
+      put(&dp.wshift, sizeof dp.wshift);
+    }
+  }
+  return k;
+}
+
+int setup_green(flups_solver_s* s, cudaStream_t st) {
+  int du = 0;
+  for (int d = 0; d < 3; ++d) du += s->dir[d].unb;
+  const bool stored = du > 0 || s->topo.prec == FLUPS_F64E;
+  if (!s->share_green || !stored) return setup_green_compute(s, st);
+  const std::string key = green_cache_key(s);
+  {
+    std::lock_guard<std::mutex> lk(g_green_mu);
+    auto it = g_green_cache.find(key);
+    if (it != g_green_cache.end()) {
+      it->second.refs++;
+      s->green_dev = it->second.dev;
+      s->green_pitch = it->second.pitch;
+      s->green_bytes = it->second.bytes;
+      s->green_key = key;
+      return FLUPS_OK;
+    }
+  }
+  const int rc = setup_green_compute(s, st);
+  if (rc || !s->green_dev) return rc;
+  std::lock_guard<std::mutex> lk(g_green_mu);
+  auto it = g_green_cache.find(key);
+  if (it != g_green_cache.end()) {
+    // another solver stored the same spectrum meanwhile: use that copy
+    cudaFreeAsync(s->green_dev, st);
+    it->second.refs++;
+    s->green_dev = it->second.dev;
+    s->green_pitch = it->second.pitch;
+  } else {
+    const size_t padded = (size_t)s->green_pitch * s->dir[1].gext * s->dir[2].gext * esize(s->topo.prec);
+    g_green_cache[key] = GreenEntry{s->green_dev, s->green_pitch, s->green_bytes, padded, 1};
+  }
+  s->green_key = key;
   return FLUPS_OK;
 }
 
@@ -1194,6 +1271,16 @@ static void release(flups_solver s, cudaStream_t st, bool async) {
   }
   fr(s->W1);
   fr(s->W2);
+  if (!s->green_key.empty()) {
+    std::lock_guard<std::mutex> lk(g_green_mu);
+    auto it = g_green_cache.find(s->green_key);
+    if (it != g_green_cache.end() && --it->second.refs == 0) {
+      fr(it->second.dev);
+      g_green_cache.erase(it);
+    }
+    s->green_dev = nullptr;
+    s->green_key.clear();
+  }
   fr(s->green_dev);
   fr(s->stage);
   fr(s->errflag);
@@ -1214,6 +1301,13 @@ int flups_cleanup_async(flups_solver s, void* stream) {
   if (!s) return FLUPS_OK;
   release(s, (cudaStream_t)stream, true);
   delete s;
+  return FLUPS_OK;
+}
+
+int flups_solver_share_green(flups_solver s) {
+  if (!s) return FLUPS_EINVAL;
+  if (s->ready) return FLUPS_ESTATE;
+  s->share_green = true;
   return FLUPS_OK;
 }
 

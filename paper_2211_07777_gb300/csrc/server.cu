@@ -230,6 +230,8 @@ int new_plan(const flups_request& r, Plan** out) {
   int rc = flups_init_topo(r.n, r.center, ncomp_of(r), r.prec, &p->topo);
   if (rc == FLUPS_OK)
     rc = flups_init_solver(p->topo, &r.bc[0][0][0], r.h, r.L, r.green, r.eps_over_h, r.op, r.diff, &p->solver);
+  // plans of other face conditions often store the same Green spectrum: one copy for all of them
+  if (rc == FLUPS_OK) rc = flups_solver_share_green(p->solver);
   if (rc == FLUPS_OK) rc = flups_solver_memory(p->solver, &p->resident, &p->transient, &p->ws);
   if (rc != FLUPS_OK) {
     if (p->solver) flups_cleanup(p->solver);

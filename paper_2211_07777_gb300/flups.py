@@ -30,6 +30,7 @@ EXPORTED = (
     "flups_setup_shared", "flups_cleanup_async", "flups_workspace_size", "flups_solve_ws", "flups_solver_memory",
     "flups_server_create", "flups_server_submit", "flups_server_poll", "flups_server_wait", "flups_server_pending",
     "flups_server_get_stats", "flups_server_destroy", "flups_solver_check", "flups_pass_features",
+    "flups_solver_share_green",
 )
 
 
@@ -90,6 +91,7 @@ def lib():
         L.flups_solve_ws.argtypes = [vp, vp, vp, vp, vp]
         L.flups_solver_memory.argtypes = [vp, szp, szp, szp]
         L.flups_solver_check.argtypes = [vp, ip]
+        L.flups_solver_share_green.argtypes = [vp]
         L.flups_pass_features.argtypes = [vp, ctypes.c_int, ip]
         llp = ctypes.POINTER(ctypes.c_longlong)
         L.flups_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]
@@ -323,7 +325,7 @@ class Solver:
     """One planned solve: Solver(n, bc, h=..., ...) then solve(phi, rhs) on CUDA tensors."""
 
     def __init__(self, n, bc, L=(1.0, 1.0, 1.0), center=CELL, prec=F64, green="spectral", eps_over_h=2.0,
-                 op=POISSON, diff=DIFF_SPECTRAL, ncomp=None, h=None, stream=None):
+                 op=POISSON, diff=DIFF_SPECTRAL, ncomp=None, h=None, stream=None, share_green=False):
         if ncomp is None:
             ncomp = 3 if op == BIOT_SAVART else 1
         self.n = tuple(int(v) for v in n)
@@ -341,6 +343,8 @@ class Solver:
             flups_topo_free(self._topo)
             self._topo = None
             raise
+        if share_green:
+            _check(lib().flups_solver_share_green(self._s), "flups_solver_share_green")
         self.workspace_bytes = flups_setup(self._s, stream)
         self.info = flups_solver_info(self._s)
 

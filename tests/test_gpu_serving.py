@@ -145,3 +145,38 @@ def test_seeded_stream_replays_identically():
     b = serve.run_stream(reqs, 128 << 20, nstreams=3, time_scale=0.5, keep=keep)
     for rid in keep:
         assert np.array_equal(a["outputs"][rid].numpy(), b["outputs"][rid].numpy())
+
+
+def test_shared_green_spectrum_outlives_the_first_solver():
+    """Solvers that opt in share one stored Green spectrum when their data are the same (here x
+    even-even vs odd-odd: both half-wave); releasing one leaves the other's results intact."""
+    import torch
+    import oracle
+    U, P, E, O = F.UNB, F.PER, F.EVEN, F.ODD
+    n = (32, 24, 16)
+    h = tuple(1.0 / v for v in n)
+    rng = np.random.default_rng(81)
+    f = rng.standard_normal((n[2], n[1], n[0]))
+    bcs = [((E, E), (P, P), (U, U)), ((O, O), (P, P), (U, U))]
+    refs = [oracle.solve(f, oracle.Problem(bc=bc, h=h, center=oracle.CELL, kernel="hej2")) for bc in bcs]
+    sols = [F.Solver(n, bc, prec=F.F64, green="hej2", share_green=True) for bc in bcs]
+    rhs = torch.from_numpy(f).to("cuda", torch.float64)
+
+    def run(s):
+        phi = torch.empty_like(rhs)
+        s.solve(phi, rhs)
+        torch.cuda.synchronize()
+        assert s.check() == 0
+        return phi.cpu().numpy()
+
+    try:
+        for s, ref in zip(sols, refs):
+            assert np.abs(run(s) - ref).max() <= 1e-12 * np.abs(ref).max()
+        sols[0].close()
+        again = F.Solver(n, bcs[0], prec=F.F64, green="hej2", share_green=True)   # a third user
+        assert np.abs(run(sols[1]) - refs[1]).max() <= 1e-12 * np.abs(refs[1]).max()
+        assert np.abs(run(again) - refs[0]).max() <= 1e-12 * np.abs(refs[0]).max()
+        again.close()
+    finally:
+        for s in sols:
+            s.close()
