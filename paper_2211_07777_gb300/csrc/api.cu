@@ -718,7 +718,7 @@ bool green_tensor_maps(flups_solver_s* s, int axis, int W, int P, int prec, int*
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
   }
-  if (!s->gmaps_dev && cudaMalloc(&s->gmaps_dev, sizeof(maps)) != cudaSuccess) {
+  if (!s->gmaps_dev && cudaMallocAsync(&s->gmaps_dev, sizeof(maps), st) != cudaSuccess) {
     cudaGetLastError();
     s->gmaps_dev = nullptr;
     return false;
@@ -1284,10 +1284,7 @@ static void release(flups_solver s, cudaStream_t st, bool async) {
   fr(s->green_dev);
   fr(s->stage);
   fr(s->errflag);
-  if (s->gmaps_dev) {
-    cudaFree(s->gmaps_dev);
-    s->gmaps_dev = nullptr;
-  }
+  fr(s->gmaps_dev);
 }
 
 int flups_cleanup(flups_solver s) {
