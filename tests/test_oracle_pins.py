@@ -195,6 +195,21 @@ def test_printed_semi_unbounded(kernel, npts):
     _check_printed(err, _G["semi_unbounded"][kernel][npts])
 
 
+@pytest.mark.parametrize("case,kernel", [("unbounded", "hej4"), ("semi_unbounded", "hej2")])
+def test_printed_at_129_points(case, kernel):
+    """One kernel of each validation case at the next printed resolution (N + 1 = 129)."""
+    N = 128
+    h = 1.0 / N
+    if case == "unbounded":
+        phi, f = analytic.case_unbounded(N)
+        bc = ((UNB, UNB),) * 3
+    else:
+        phi, f = analytic.case_semi_unbounded(N)
+        bc = ((UNB, EVEN), (UNB, UNB), (ODD, UNB))
+    err = np.abs(solve(f, Problem(bc=bc, h=(h, h, h), center=NODE, kernel=kernel)) - phi).max()
+    _check_printed(err, _G[case][kernel]["129"])
+
+
 # ---------------------------------------------------------------------------
 # 3. Kernels against quadrature of their integral definitions.
 # ---------------------------------------------------------------------------
