@@ -108,10 +108,18 @@ int flups_setup(flups_solver s, void* stream, size_t* workspace_bytes);
  * read-only unless phi == rhs. */
 int flups_solve(flups_solver s, void* phi, const void* rhs, void* stream);
 
-/* Same solve with HOST arrays: copies rhs host->device, solves, copies the
- * result device->host, all on `stream`, and synchronises it.  Pinned host
- * memory gives full copy bandwidth; pageable memory works. */
+/* Same solve with HOST arrays, on `stream`, synchronised before returning.
+ * A pinned array (cudaHostAlloc / cudaHostRegister, mapped into the unified
+ * address space; flups_host_mapped says so) is used in place: the first pass
+ * loads rhs, and the last pass stores phi, over the host link, so the
+ * transfers overlap those two passes.  A pageable array goes through a device
+ * staging copy (allocated on first use, kept with the solver).  phi_host ==
+ * rhs_host is allowed. */
 int flups_solve_host(flups_solver s, void* phi_host, const void* rhs_host, void* stream);
+
+/* 1 if the host range [host, host + bytes) is pinned memory that the device
+ * addresses directly (what flups_solve_host uses in place), else 0. */
+int flups_host_mapped(const void* host, size_t bytes);
 
 /* Releases the plan, the Green spectrum and the workspace (twiddle tables
  * are shared by all solvers of the process and kept until exit).  The

@@ -1236,11 +1236,39 @@ int flups_pass_features(flups_solver s, int i, int* flags) {
   return FLUPS_OK;
 }
 
+// Device address of a host range [p, p + bytes) that the device can load from and store to
+// directly: pinned memory (cudaHostAlloc, cudaHostRegister), mapped into the unified address
+// space, checked at both ends of the range.  nullptr for pageable memory or a range that leaves
+// its pinned allocation.
+static void* mapped_device_ptr(const void* p, size_t bytes) {
+  if (!p || bytes == 0) return nullptr;
+  cudaPointerAttributes a{}, b{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  const char* last = (const char*)p + (bytes - 1);
+  if (cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (b.type != cudaMemoryTypeHost || (const char*)b.devicePointer != (const char*)a.devicePointer + (bytes - 1))
+    return nullptr;
+  return a.devicePointer;
+}
+
+int flups_host_mapped(const void* host, size_t bytes) { return mapped_device_ptr(host, bytes) ? 1 : 0; }
+
 int flups_solve_host(flups_solver s, void* phi_host, const void* rhs_host, void* stream) {
   if (!s || !phi_host || !rhs_host) return FLUPS_EINVAL;
   if (!s->ready || s->shared) return FLUPS_ESTATE;
   cudaStream_t st = (cudaStream_t)stream;
-  if (!s->stage) {
+  // Pinned arrays are used in place: the first pass loads rhs and the last pass stores phi across
+  // the host link, so the transfers run inside the two x passes instead of before and after them.
+  const void* rin = mapped_device_ptr(rhs_host, s->user_bytes);
+  void* rout = mapped_device_ptr(phi_host, s->user_bytes);
+  if ((!rin || !rout) && !s->stage) {
     cudaError_t e = cudaMalloc(&s->stage, s->user_bytes);
     if (e == cudaErrorMemoryAllocation) {
       cudaGetLastError();
@@ -1249,10 +1277,13 @@ int flups_solve_host(flups_solver s, void* phi_host, const void* rhs_host, void*
     if (e) return cuda_fail(e, "stage alloc");
     s->ws_bytes += s->user_bytes;
   }
-  CK(cudaMemcpyAsync(s->stage, rhs_host, s->user_bytes, cudaMemcpyHostToDevice, st));
-  int rc = flups_solve(s, s->stage, s->stage, stream);
+  if (!rin) {
+    CK(cudaMemcpyAsync(s->stage, rhs_host, s->user_bytes, cudaMemcpyHostToDevice, st));
+    rin = s->stage;
+  }
+  int rc = flups_solve(s, rout ? rout : s->stage, rin, stream);
   if (rc) return rc;
-  CK(cudaMemcpyAsync(phi_host, s->stage, s->user_bytes, cudaMemcpyDeviceToHost, st));
+  if (!rout) CK(cudaMemcpyAsync(phi_host, s->stage, s->user_bytes, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return FLUPS_OK;
 }

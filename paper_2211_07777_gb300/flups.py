@@ -30,7 +30,7 @@ EXPORTED = (
     "flups_setup_shared", "flups_cleanup_async", "flups_workspace_size", "flups_solve_ws", "flups_solver_memory",
     "flups_server_create", "flups_server_submit", "flups_server_poll", "flups_server_wait", "flups_server_pending",
     "flups_server_get_stats", "flups_server_destroy", "flups_solver_check", "flups_pass_features",
-    "flups_solver_share_green",
+    "flups_solver_share_green", "flups_host_mapped",
 )
 
 
@@ -91,6 +91,7 @@ def lib():
         L.flups_solve_ws.argtypes = [vp, vp, vp, vp, vp]
         L.flups_solver_memory.argtypes = [vp, szp, szp, szp]
         L.flups_solver_check.argtypes = [vp, ip]
+        L.flups_host_mapped.argtypes = [vp, ctypes.c_size_t]
         L.flups_solver_share_green.argtypes = [vp]
         L.flups_pass_features.argtypes = [vp, ctypes.c_int, ip]
         llp = ctypes.POINTER(ctypes.c_longlong)
@@ -181,6 +182,14 @@ def flups_solve(solver, phi, rhs, stream=None):
 
 def flups_solve_host(solver, phi_host, rhs_host, stream=None):
     _check(lib().flups_solve_host(solver, _ptr(phi_host), _ptr(rhs_host), _stream(stream)), "flups_solve_host")
+
+
+def flups_host_mapped(host, nbytes=None):
+    """True if the host array (or nbytes from its address) is pinned memory the device addresses
+    directly, i.e. flups_solve_host uses it in place."""
+    if nbytes is None:
+        nbytes = host.numel() * host.element_size() if hasattr(host, "element_size") else host.nbytes
+    return bool(lib().flups_host_mapped(_ptr(host), nbytes))
 
 
 def flups_cleanup(solver):
@@ -378,6 +387,12 @@ class Solver:
         code = ctypes.c_int(0)
         _check(lib().flups_solver_check(self._s, ctypes.byref(code)), "flups_solver_check")
         return code.value
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
     def close(self):
         if getattr(self, "_s", None) is not None:
