@@ -33,7 +33,7 @@ def _host(f, dt, pinned):
 def test_host_solve_matches_device_solve(prec, pin_in, pin_out):
     import torch
     dt = torch.float32 if prec == F.F32 else torch.float64
-    shape = (24, 20, 32)
+    shape = (24, 12, 32)
     f = np.random.default_rng(3).standard_normal(shape)
     bc = ((U, U), (E, O), (PER, PER))
     n = (shape[2], shape[1], shape[0])
