@@ -594,11 +594,20 @@ __device__ __forceinline__ void xstages(cpx<T>* S, cpx<T>* v, const cpx<T>* __re
   }
 }
 
+// Launch order of the fused column pass along its other direction: 0, 1, n-1, 2, n-2, ... (a
+// bijection of [0, n)).  Rows o and n - o read the same folded Green slice, so the CTAs that share
+// it run back to back and the second read comes from L2.
+__device__ __forceinline__ int mirror_order(int b, int n) {
+  if (b == 0) return 0;
+  const int k = (b + 1) >> 1;
+  return (b & 1) ? k : n - k;
+}
+
 template <typename T>
-__device__ __forceinline__ ColIO<T> col_io(const PassParams& p, int W, int n_in, int n_out, int dup) {
+__device__ __forceinline__ ColIO<T> col_io(const PassParams& p, int W, int n_in, int n_out, int dup, int o) {
   ColIO<T> io;
-  const long long obase_i = (long long)blockIdx.y * p.ai.os + (long long)blockIdx.z * p.ai.cs;
-  const long long obase_o = (long long)blockIdx.y * p.ao.os + (long long)blockIdx.z * p.ao.cs;
+  const long long obase_i = (long long)o * p.ai.os + (long long)blockIdx.z * p.ai.cs;
+  const long long obase_o = (long long)o * p.ao.os + (long long)blockIdx.z * p.ao.cs;
   io.in = (const cpx<T>*)p.in + obase_i;
   io.out = (cpx<T>*)p.out + obase_o;
   io.ils = p.ai.ls;
@@ -624,9 +633,9 @@ __device__ __forceinline__ unsigned char* col_base(unsigned char* smraw) {
 // rows into the dense tile S (row i of lane l at S[i W + l]); rows past the array's extent arrive
 // as zeros.  p must be the kernel's __grid_constant__ parameter (the map is read in place).
 template <typename T, int W>
-__device__ __forceinline__ void tile_tma_issue(const PassParams& p, cpx<T>* S, unsigned long long* bar) {
+__device__ __forceinline__ void tile_tma_issue(const PassParams& p, cpx<T>* S, unsigned long long* bar, int o) {
   constexpr int U = (int)sizeof(cpx<T>) / 8;  // 8-byte units per element
-  const int q0 = blockIdx.x * W, o = blockIdx.y, c = blockIdx.z;
+  const int q0 = blockIdx.x * W, c = blockIdx.z;
   mbar_expect_tx(bar, (unsigned)((size_t)p.tin_rows * W * sizeof(cpx<T>)));
   for (int r0 = 0; r0 < p.tin_rows; r0 += p.tin_box) {
     if (p.axis == 1) tma_load_4d(S + (size_t)r0 * W, &p.tin, q0 * U, r0, o, c, bar);
@@ -643,12 +652,12 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   cpx<T>* S = reinterpret_cast<cpx<T>*>(base);
   cpx<T> v[16];
   const int tid = threadIdx.x;
-  const ColIO<T> io = col_io<T>(p, WC, p.n_use, PC, -1);
+  const ColIO<T> io = col_io<T>(p, WC, p.n_use, PC, -1, blockIdx.y);
   const cpx<T>* tw = (const cpx<T>*)p.tw;
   if (p.tin_rows) {
     if (tid == 0) mbar_init(mbar_in, 1);
     __syncthreads();
-    if (tid == 0) tile_tma_issue<T, WC>(p, S, mbar_in);
+    if (tid == 0) tile_tma_issue<T, WC>(p, S, mbar_in, blockIdx.y);
     mbar_wait_bounded(mbar_in, p.errflag, 2);
     xstages<T, PC, WC, false, false, 0, XS_NAT, XS_GLOBAL, HZ, false>(S, v, tw, tid, io);
   } else {
@@ -666,12 +675,12 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   cpx<T> v[16];
   const int tid = threadIdx.x;
   const int dup = (p.type == T_PER && p.center == C_NODE && p.n_data > p.N) ? p.N : -1;
-  const ColIO<T> io = col_io<T>(p, WC, PC, p.n_data, dup);
+  const ColIO<T> io = col_io<T>(p, WC, PC, p.n_data, dup, blockIdx.y);
   const cpx<T>* tw = (const cpx<T>*)p.tw;
   if (p.tin_rows) {
     if (tid == 0) mbar_init(mbar_in, 1);
     __syncthreads();
-    if (tid == 0) tile_tma_issue<T, WC>(p, S, mbar_in);
+    if (tid == 0) tile_tma_issue<T, WC>(p, S, mbar_in, blockIdx.y);
     mbar_wait_bounded(mbar_in, p.errflag, 2);
     xstages<T, PC, WC, true, false, 0, XS_NAT, XS_GLOBAL, false, HZ>(S, v, tw, tid, io);
   } else {
@@ -697,6 +706,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   constexpr int GH = P / 2 + 1;
   const int tid = threadIdx.x;
   const int q0 = blockIdx.x * W;
+  const int o = mirror_order(blockIdx.y, gridDim.y);
   const bool tma_g = p.gpre && p.gmap;
   // TMA copies: the input tile (p.tin_rows) and the Green slice (p.gmap), each completed on its
   // own mbarrier; thread 0 initialises both before the CTA barrier and then issues the loads
@@ -707,11 +717,10 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     }
     __syncthreads();
     if (tid == 0) {
-      if (p.tin_rows) tile_tma_issue<T, W>(p, S, mbar_in);
+      if (p.tin_rows) tile_tma_issue<T, W>(p, S, mbar_in, o);
       if (tma_g) {
         const FusedGreen& g = p.g;
-        const int nd = p.axis == 2 ? 1 : 2;  // the direction blockIdx.y runs along
-        const int o = blockIdx.y;
+        const int nd = p.axis == 2 ? 1 : 2;  // the direction o runs along
         const int go = g.fold[nd] ? min(o, g.fold[nd] - o) : o;
         const char* maps = (const char*)p.gmap;
         mbar_expect_tx(mbar_g, (unsigned)(GH * W * sizeof(T)));
@@ -730,7 +739,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     const int lane = tid % W;
     long long go;
     T kp;
-    pencil_green_base<T>(p, q0 + lane, blockIdx.y, &go, &kp);
+    pencil_green_base<T>(p, q0 + lane, o, &go, &kp);
     if (q0 + lane < p.npen) {
       const long long st3 = p.axis == 1 ? (long long)p.g.gpitch : (long long)p.g.gpitch * p.g.gext[1];
       const T* src = (const T*)p.g.stored + go;
@@ -738,10 +747,10 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     }
     cp_async_commit();
   } else if (!p.gpre) {
-    for (int lane = tid; lane < W; lane += NT) pencil_green_base<T>(p, q0 + lane, blockIdx.y, &goff[lane], &k2p[lane]);
+    for (int lane = tid; lane < W; lane += NT) pencil_green_base<T>(p, q0 + lane, o, &goff[lane], &k2p[lane]);
   }
   const int dup = (p.type == T_PER && p.center == C_NODE && p.n_data > p.N) ? p.N : -1;
-  const ColIO<T> io = col_io<T>(p, W, p.n_use, p.n_data, dup);
+  const ColIO<T> io = col_io<T>(p, W, p.n_use, p.n_data, dup, o);
   const cpx<T>* tw = (const cpx<T>*)p.tw;
   cpx<T> v[16];
   // forward: HBM (or the TMA tile) -> ... -> registers (the first stage's barrier also publishes goff/k2p)
