@@ -28,6 +28,11 @@ What it computes (Section "Methodology"):
    original samples.  Node-centred boundary values are then set as the paper
    states: periodic phi_N := phi_0; an odd face holds 0.
 
+The Biot-Savart variant (``biot_savart``, Section "Biot-Savart solver") takes
+the curl in Fourier space on the extended signals with the spectral symbol or
+the finite-difference symbols of orders 2, 4 and 6; the tests pin those
+against real-space central-difference stencils and their convergence orders.
+
 Everything is FP64.  Arrays are indexed [z, y, x] (x fastest, C order);
 direction d = 0, 1, 2 (x, y, z) is numpy axis 2 - d.
 """

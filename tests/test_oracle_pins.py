@@ -571,3 +571,57 @@ def test_biot_savart_symmetric_unbounded_matches_scalar_solves():
     assert np.abs(out[0] - ux).max() < 2e-3 * scale
     assert np.abs(out[1] - uy).max() < 2e-3 * scale
     assert np.abs(out[2]).max() < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# Finite-difference derivative symbols of the Biot-Savart curl (Section
+# "Biot-Savart solver": orders 2, 4 and 6) against real-space central
+# differences with the textbook stencil weights, and against their order.
+# ---------------------------------------------------------------------------
+_STENCILS = {"fd2": (1.0 / 2.0,), "fd4": (2.0 / 3.0, -1.0 / 12.0), "fd6": (3.0 / 4.0, -3.0 / 20.0, 1.0 / 60.0)}
+
+
+def _curl_stencil(f, h, weights):
+    """Curl of a periodic [c, z, y, x] field, d/dx_d a = sum_m w_m (a_{j+m} - a_{j-m}) / h_d."""
+    def d(a, direction):
+        ax = 2 - direction
+        out = np.zeros_like(a)
+        for m, w in enumerate(weights, start=1):
+            out += w * (np.roll(a, -m, axis=ax) - np.roll(a, m, axis=ax)) / h[direction]
+        return out
+    fx, fy, fz = f
+    return np.stack([d(fz, 1) - d(fy, 2), d(fx, 2) - d(fz, 0), d(fy, 0) - d(fx, 1)])
+
+
+@pytest.mark.parametrize("diff", ["fd2", "fd4", "fd6"])
+def test_finite_difference_curl_is_the_central_stencil(diff):
+    """Periodic grid: u of the FD Biot-Savart solve = the Poisson solves of the stencil curl."""
+    rng = np.random.default_rng(61)
+    f = rng.standard_normal((3, 8, 12, 16))
+    h = (1.0 / 16, 1.0 / 12, 1.0 / 8)
+    bc = ((PER, PER),) * 3
+    u = oracle.biot_savart(f, (bc, bc, bc), h, center=CELL, kernel="spectral", diff=diff)
+    c = _curl_stencil(f, h, _STENCILS[diff])
+    want = np.stack([solve(c[i], Problem(bc=bc, h=h, center=CELL, kernel="spectral")) for i in range(3)])
+    assert np.abs(u - want).max() < 1e-13 * np.abs(want).max()
+
+
+def test_finite_difference_orders():
+    """A smooth periodic field: the FD velocity approaches the spectral one as h^2, h^4, h^6."""
+    def field(n):
+        x = (np.arange(n) + 0.5) / n
+        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+        s = 2 * math.pi
+        return np.stack([np.sin(s * Y) * np.cos(s * Z), np.sin(s * Z) * np.cos(2 * s * X), np.cos(s * X) * np.sin(s * Y)])
+    bc = ((PER, PER),) * 3
+    errs = {k: [] for k in _STENCILS}
+    for n in (32, 64):
+        f = field(n)
+        h = (1.0 / n,) * 3
+        ref = oracle.biot_savart(f, (bc, bc, bc), h, center=CELL, kernel="spectral", diff="spectral")
+        for k in _STENCILS:
+            u = oracle.biot_savart(f, (bc, bc, bc), h, center=CELL, kernel="spectral", diff=k)
+            errs[k].append(np.abs(u - ref).max())
+    for k, p in (("fd2", 2), ("fd4", 4), ("fd6", 6)):
+        rate = math.log2(errs[k][0] / errs[k][1])
+        assert abs(rate - p) < 0.1, (k, rate)
