@@ -130,6 +130,13 @@ int flups_host_mapped(const void* host, size_t bytes);
 int flups_cleanup(flups_solver s);
 int flups_cleanup_async(flups_solver s, void* stream);
 
+/* The planner's transform order (host-only, any time after flups_init_solver):
+ * order[i] = the direction (0 x, 1 y, 2 z) transformed i-th, by cost class
+ * (Section 1: symmetric, then semi-unbounded, then periodic, then unbounded),
+ * ties in x, y, z order; the first periodic or unbounded direction in that
+ * order takes the real-to-complex transform. */
+int flups_solver_order(flups_solver s, int order[3]);
+
 /* Introspection (host-only, after flups_setup): number of kernel launches per
  * solve; transform order (3 direction indices); algorithmic bytes moved per
  * solve by the 5-pass model (each pass reads and writes its arrays once plus

@@ -1349,6 +1349,12 @@ int flups_solver_check(flups_solver s, int* code) {
   return FLUPS_OK;
 }
 
+int flups_solver_order(flups_solver s, int order[3]) {
+  if (!s || !order) return FLUPS_EINVAL;
+  for (int i = 0; i < 3; ++i) order[i] = s->order[i];
+  return FLUPS_OK;
+}
+
 int flups_solver_info(flups_solver s, int* launches_per_solve, int order[3], double* model_bytes, double* green_bytes) {
   if (!s) return FLUPS_EINVAL;
   if (!s->ready) return FLUPS_ESTATE;

@@ -30,7 +30,7 @@ EXPORTED = (
     "flups_setup_shared", "flups_cleanup_async", "flups_workspace_size", "flups_solve_ws", "flups_solver_memory",
     "flups_server_create", "flups_server_submit", "flups_server_poll", "flups_server_wait", "flups_server_pending",
     "flups_server_get_stats", "flups_server_destroy", "flups_solver_check", "flups_pass_features",
-    "flups_solver_share_green", "flups_host_mapped",
+    "flups_solver_share_green", "flups_host_mapped", "flups_solver_order",
 )
 
 
@@ -92,6 +92,7 @@ def lib():
         L.flups_solver_memory.argtypes = [vp, szp, szp, szp]
         L.flups_solver_check.argtypes = [vp, ip]
         L.flups_host_mapped.argtypes = [vp, ctypes.c_size_t]
+        L.flups_solver_order.argtypes = [vp, ip]
         L.flups_solver_share_green.argtypes = [vp]
         L.flups_pass_features.argtypes = [vp, ctypes.c_int, ip]
         llp = ctypes.POINTER(ctypes.c_longlong)
@@ -182,6 +183,13 @@ def flups_solve(solver, phi, rhs, stream=None):
 
 def flups_solve_host(solver, phi_host, rhs_host, stream=None):
     _check(lib().flups_solve_host(solver, _ptr(phi_host), _ptr(rhs_host), _stream(stream)), "flups_solve_host")
+
+
+def flups_solver_order(solver):
+    """The planner's transform order: the directions (0 x, 1 y, 2 z) in the order they are transformed."""
+    order = (ctypes.c_int * 3)()
+    _check(lib().flups_solver_order(solver, order), "flups_solver_order")
+    return tuple(order)
 
 
 def flups_host_mapped(host, nbytes=None):

@@ -97,3 +97,41 @@ def test_solve_before_setup_is_a_state_error(lib):
     assert e.value.status == -7
     F.flups_cleanup(s)
     F.flups_topo_free(t)
+
+
+_FACES = {"PER": ("PER", "PER"), "UNB": ("UNB", "UNB"), "EE": ("EVEN", "EVEN"), "EO": ("EVEN", "ODD"),
+          "OE": ("ODD", "EVEN"), "OO": ("ODD", "ODD"), "EU": ("EVEN", "UNB"), "OU": ("ODD", "UNB"),
+          "UE": ("UNB", "EVEN"), "UO": ("UNB", "ODD")}
+
+
+def _plan_order(F, types):
+    bc = tuple(tuple(getattr(F, f) for f in _FACES[t]) for t in types)
+    t = F.flups_init_topo((16, 16, 16), 0, 1, F.F64)
+    try:
+        s = F.flups_init_solver(t, bc, (1 / 16,) * 3, (1.0,) * 3, "hej2")
+        try:
+            return F.flups_solver_order(s)
+        finally:
+            F.flups_cleanup(s)
+    finally:
+        F.flups_topo_free(t)
+
+
+@pytest.mark.parametrize("types,want", [
+    (("UNB", "EE", "PER"), (1, 2, 0)),   # symmetric, then periodic, then unbounded
+    (("PER", "PER", "PER"), (0, 1, 2)),  # ties keep x, y, z
+    (("UE", "OO", "UNB"), (1, 0, 2)),    # symmetric < semi-unbounded < unbounded
+    (("UNB", "UNB", "EO"), (2, 0, 1)),
+    (("PER", "OU", "EE"), (2, 1, 0)),
+])
+def test_plan_order_follows_the_cost_classes(lib, types, want):
+    """Section 1: directions are transformed cheapest first — symmetric, semi-unbounded,
+    periodic, unbounded — ties in x, y, z order."""
+    assert _plan_order(lib, types) == want
+
+
+def test_plan_order_matches_the_oracle_for_every_type_triple(lib):
+    import itertools
+    import oracle
+    for types in itertools.product(list(_FACES), repeat=3):
+        assert _plan_order(lib, types) == tuple(oracle.direction_order(types)), types
