@@ -44,7 +44,8 @@ typedef enum {
   FLUPS_ENOMEM = -4,   /* device or host allocation failed */
   FLUPS_ECUDA = -5,    /* a CUDA runtime call failed (see flups_last_cuda_error) */
   FLUPS_EGREEN = -6,   /* Green kernel not available for these boundary conditions */
-  FLUPS_ESTATE = -7    /* call out of order (e.g. solve before setup) */
+  FLUPS_ESTATE = -7,   /* call out of order (e.g. solve before setup) */
+  FLUPS_EDEVICE = -8   /* a kernel's bounded wait gave up (see flups_solver_check): the result is not valid */
 } flups_status;
 
 /* Face conditions (Section 2.2, 2.3). */
@@ -160,7 +161,8 @@ int flups_solve_events(flups_solver s, void* phi, const void* rhs, void* stream,
 int flups_pass_info(flups_solver s, int i, int* kind, int* axis, int* fft_len, double* bytes, double* flops);
 /* How pass i runs (bit flags): 1 compile-time tile engine, 2 Green slice staged in shared memory
  * ahead of the multiply, 4 that slice copied by TMA (tensor map + mbarrier), 8 doubled transform
- * pruned to its nonzero half.  Introspection only; no counterpart in the paper. */
+ * pruned to its nonzero half, 16 input tile copied by TMA (tensor map + mbarrier).  Introspection
+ * only; no counterpart in the paper. */
 int flups_pass_features(flups_solver s, int i, int* flags);
 
 /* Allocation-free fully periodic solve (the paper has no counterpart; this is
@@ -194,9 +196,17 @@ int flups_solve_periodic_noalloc(double* phi, const double* rhs, const int n[3],
  * spectrum) serves any number of solves in flight on different streams, each
  * with its own workspace.  flups_solver_memory (host-only, after
  * flups_init_solver): device bytes the plan keeps resident, the transient
- * peak of its setup, and the workspace of one solve. */
+ * peak of its setup, and the workspace of one solve.
+ *
+ * Device status of a workspace solve: the int at byte offset
+ * flups_workspace_status(s) of the workspace is zeroed at the start of each
+ * flups_solve_ws (stream-ordered) and set to a nonzero code by a kernel whose
+ * bounded wait gave up (codes as in flups_solver_check); read it after the
+ * solve has completed, e.g. with a stream-ordered copy to the host.  Each
+ * workspace thus reports the status of its own solve. */
 int flups_setup_shared(flups_solver s, void* stream);
 int flups_workspace_size(flups_solver s, size_t* bytes);
+int flups_workspace_status(flups_solver s, size_t* offset);
 int flups_solve_ws(flups_solver s, void* phi, const void* rhs, void* workspace, void* stream);
 int flups_solver_memory(flups_solver s, size_t* resident, size_t* transient, size_t* workspace);
 
@@ -235,14 +245,24 @@ int flups_server_submit(flups_server sv, const flups_request* rq, const void* rh
                         long long* ticket);
 /* Completed tickets since the last call (up to max): latency from submission
  * to the end of the result's copy to the host, in seconds, and the status
- * (FLUPS_OK, or an error with latency -1).  poll never blocks; wait blocks
- * until at least one ticket completes or nothing is left. */
+ * (FLUPS_OK, or an error with latency -1; FLUPS_EDEVICE when a kernel of that
+ * request's own solve reported a bounded wait that gave up, so its phi is not
+ * valid).  poll never blocks; wait blocks until at least one ticket completes
+ * or nothing is left. */
 int flups_server_poll(flups_server sv, long long* tickets, double* latency_s, int* status, int max, int* n_done);
 int flups_server_wait(flups_server sv, long long* tickets, double* latency_s, int* status, int max, int* n_done);
 int flups_server_pending(flups_server sv, int* queued, int* running);
 int flups_server_get_stats(flups_server sv, flups_server_stats* out);
 /* Waits for the requests in flight, then frees every plan, slot and stream. */
 int flups_server_destroy(flups_server sv);
+
+/* Measured fused multiply-add rate of the current device (measurement support;
+ * the paper has no counterpart): prec = FLUPS_F32 or FLUPS_F64; one launch of
+ * 8 CTAs per SM, 256 threads each running 8 independent FMA chains for
+ * 16 * iters steps, timed with CUDA events after a warm-up launch.
+ * *tflops = 2 * FMAs / time (TFLOP/s), *ms (may be NULL) = the timed launch.
+ * Allocates and frees a small device buffer; synchronous. */
+int flups_measure_fma_peak(int prec, int iters, double* tflops, double* ms);
 
 /* Text of a status code (static storage). */
 const char* flups_strerror(int status);
@@ -257,12 +277,39 @@ const char* flups_last_cuda_error(void);
  * (the serving runtime releases idle plans only).  No counterpart in the paper. */
 int flups_solver_share_green(flups_solver s);
 
-/* Device-side status of the solver's kernels since the last call: *code = 0, or
- * the nonzero code a kernel left when one of its bounded waits gave up (1: the
- * TMA copy of the Green slice in the fused pass did not complete in time; the
- * solve's result is then not valid).  Synchronises the device, resets the code.
- * No counterpart in the paper (device-side failure reporting). */
+/* Device-side status of the solver's kernels (solves on its own workspace)
+ * since the last call: *code = 0, or the nonzero code a kernel left when one
+ * of its bounded waits gave up: 1 the TMA copy of the Green slice in the fused
+ * pass, 2 the TMA copy of a column pass's input tile did not complete within
+ * 1 s.  A kernel whose wait gave up waits at most 0.1 s more for its copies in
+ * flight and then writes none of its tile's results, so the solve's result is
+ * not valid (undefined).  The first code recorded is kept.  Until the code is
+ * read here, later bounded waits of the solver's kernels give their copies
+ * 1 ms instead of 1 s.  Synchronises the device, resets the code.  No
+ * counterpart in the paper (device-side failure reporting). */
 int flups_solver_check(flups_solver s, int* code);
+
+/* Test hook for the precision of the stored Green spectrum: samples (n values)
+ * receives the FP64 real-space samples G(k_s, r_u) the setup transforms, the
+ * Green index x fastest over the extents of every direction (unbounded-like:
+ * r = g h, g = 0..M; spectral: the folded mode), and spectrum (n values) the
+ * stored spectrum as the fused pass reads it, converted to double (the
+ * double-float path stores hi + lo float pairs): the
+ * samples' DCT-I along each unbounded-like direction (Section 2.3: the kernel
+ * symmetrised on the extended domain, transformed there; computed in
+ * double-float arithmetic on the FP32 units) times prod(h_u)/(P1 P2 P3).
+ * n must be the product of the extents.  Only for solvers with a stored
+ * spectrum (some direction unbounded or semi-unbounded; else FLUPS_ESTATE).
+ * Synchronous; allocates a temporary device buffer.  No counterpart in the paper. */
+int flups_debug_green(flups_solver s, double* samples, double* spectrum, long long n);
+
+/* Test hook for that failure path: mask bit 0 (code 1) and bit 1 (code 2)
+ * make the corresponding bounded waits of this solver's later solves give up
+ * at once, as if their copies had not arrived in time (the copies do arrive:
+ * the drain waits for them, so no copy is left in flight).  The solve's result
+ * is then not valid and the code is reported.  mask = 0 restores normal
+ * solves.  Host-only.  No counterpart in the paper. */
+int flups_debug_wait_limit(flups_solver s, int mask);
 
 /* Test hook: evaluate the device FP64 special functions used by the Green's
  * function generation at n points (device arrays x, y, out): which = 0 E1(x),

@@ -26,6 +26,6 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
 """
 from .solver import (  # noqa: F401
     CELL, NODE, EVEN, ODD, PER, UNB, Problem, solve, biot_savart, curl_bc,
-    direction_type, direction_order, extend, restrict, extended_length, green_spectrum,
+    direction_type, direction_order, extend, restrict, extended_length, green_spectrum, set_fft_workers,
 )
 from . import green  # noqa: F401

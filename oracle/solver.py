@@ -203,6 +203,41 @@ class Problem:
         return self.eps_over_h * max(self.h)
 
 
+# The complex FFT the solve uses as a library step: numpy's (one thread) unless
+# set_fft_workers asked for scipy.fft with several worker threads.  Both compute
+# the same unnormalised DFT; only the library call changes, none of the method's
+# arithmetic.
+_FFT_WORKERS = 1
+
+
+def set_fft_workers(n: int) -> int:
+    """Use scipy.fft with n worker threads for the oracle's FFTs (n <= 1: numpy, one thread).
+    Returns the number of threads the FFTs will use."""
+    global _FFT_WORKERS
+    n = int(n)
+    if n > 1:
+        try:
+            import scipy.fft  # noqa: F401
+        except ImportError:
+            n = 1
+    _FFT_WORKERS = max(1, n)
+    return _FFT_WORKERS
+
+
+def _fftn(a, axes=None):
+    if _FFT_WORKERS > 1:
+        import scipy.fft
+        return scipy.fft.fftn(a, axes=axes, workers=_FFT_WORKERS)
+    return np.fft.fftn(a, axes=axes)
+
+
+def _ifftn(a):
+    if _FFT_WORKERS > 1:
+        import scipy.fft
+        return scipy.fft.ifftn(a, workers=_FFT_WORKERS)
+    return np.fft.ifftn(a)
+
+
 def _wavenumbers(P: int, h: float) -> np.ndarray:
     """Continuous wavenumber of each mode of a P-periodic extension (signed)."""
     p = np.arange(P)
@@ -259,7 +294,7 @@ def green_spectrum(prob: Problem, shape_ext) -> np.ndarray:
         raise ValueError(f"kernel {prob.kernel!r} with {du} unbounded direction(s) is not in the oracle")
     axes = tuple(2 - d for d in unb)
     vol = float(np.prod([prob.h[d] for d in unb]))
-    return (vol * np.fft.fftn(g, axes=axes)).real
+    return (vol * _fftn(g, axes=axes)).real
 
 
 def solve(f: np.ndarray, prob: Problem) -> np.ndarray:
@@ -271,7 +306,7 @@ def solve(f: np.ndarray, prob: Problem) -> np.ndarray:
         ax = 2 - d
         e = np.moveaxis(extend(np.moveaxis(e, ax, 0), types[d], prob.center), 0, ax)
     G = green_spectrum(prob, e.shape)
-    phi_e = np.fft.ifftn(G * np.fft.fftn(e)).real
+    phi_e = _ifftn(G * _fftn(e)).real
     out = phi_e
     for d in range(3):
         ax = 2 - d
@@ -324,7 +359,7 @@ def biot_savart(f3: np.ndarray, bc_f, h, center=CELL, kernel="spectral", eps_ove
     if any(x.shape != ext[0].shape for x in ext):
         raise ValueError("components extend to different periods")
     Pshape = ext[0].shape
-    F = [np.fft.fftn(x) for x in ext]
+    F = [_fftn(x) for x in ext]
     # the derivative symbols act on the extended signals (real, Hermitian spectra)
     ik = []
     for d in range(3):
@@ -353,7 +388,7 @@ def biot_savart(f3: np.ndarray, bc_f, h, center=CELL, kernel="spectral", eps_ove
     for c in range(3):
         a, b = (c + 1) % 3, (c + 2) % 3
         curl = ik[a] * F[b] - ik[b] * F[a]
-        u_e = np.fft.ifftn(G * curl).real
+        u_e = _ifftn(G * curl).real
         types_u = [direction_type(*bc_u[c][d]) for d in range(3)]
         o = u_e
         for d in range(3):

@@ -147,6 +147,7 @@ struct flups_solver_s {
   std::string green_key;        // its cache key when shared
   void* gmaps_dev = nullptr;    // TMA tensor maps of the stored spectrum (fused column pass)
   int* errflag = nullptr;       // device word set by bounded waits that give up
+  int dbg_wait = 0;             // test hook (flups_debug_wait_limit): waits that give up at once
   void* tabs[3] = {nullptr, nullptr, nullptr};
   void* stage = nullptr;  // device copy of the caller's host arrays (flups_solve_host)
   size_t user_bytes = 0;
@@ -155,7 +156,7 @@ struct flups_solver_s {
   std::vector<Launch> passes;
   bool ready = false;
   bool shared = false;    // set up without its own workspace (solves pass one in)
-  size_t ws_need = 0;     // bytes of workspace one solve needs (W1 + W2, 256-aligned)
+  size_t ws_need = 0;     // bytes of workspace one solve needs (W1 + W2, 256-aligned, + the status block)
 };
 
 namespace {
@@ -392,8 +393,48 @@ void fill_geom(Launch& L, const DirPlan& dp, int axis, const int* din, const int
   L.grid = dim3((p.npen + per_tile - 1) / per_tile, axis == 0 ? 1 : (axis == 1 ? din[2] : din[1]), ncomp);
   L.nthr = nthr;
   L.smem = (p.ct ? 1 : 2) * (size_t)dp.P * p.LS * 2 * esize(prec) + 16 * 2 * W + 16;
-  // column kernels: 128-byte alignment of the tile and a 128-byte block for their mbarriers
-  if (p.ct && axis != 0 && (L.kind == K_FWD_C2C || L.kind == K_INV_C2C || L.kind == K_FUSED_C2C)) L.smem += 256;
+  p.ept = 16;
+  if (p.ct && axis != 0 && (L.kind == K_FWD_C2C || L.kind == K_INV_C2C || L.kind == K_FUSED_C2C)) {
+    // column kernels: 128-byte alignment of the tile and a 128-byte block for their mbarriers;
+    // EPT elements per thread and stage
+    L.smem += 256;
+    p.ept = ct_col_ept(dp.P, prec);
+    L.nthr = dp.P * W / p.ept;
+  }
+}
+
+// CTAs per SM the compile-time kernels are built for (their __launch_bounds__ minimum).
+int ct_min_blocks(const PassParams& p, int nthr, int prec) {
+  if (p.ept == 32) return std::max(1, 512 / nthr);
+  return std::max(1, (prec == FLUPS_F32 ? 1024 : 512) / nthr);
+}
+
+// Sampling parameters of the stored spectrum (every direction's Green index extent, the
+// unbounded-like directions sampled in real space, the spectral ones by wavenumber).
+GreenSampleParams green_params(const flups_solver_s* s) {
+  GreenSampleParams q{};
+  int du = 0;
+  for (int d = 0; d < 3; ++d) {
+    const DirPlan& dp = s->dir[d];
+    q.gext[d] = dp.gext;
+    q.unb[d] = dp.unb;
+    q.h[d] = dp.h;
+    q.wscale[d] = dp.wscale;
+    q.wshift[d] = dp.wshift;
+    du += dp.unb;
+  }
+  q.du = du;
+  q.kernel = s->green == FLUPS_HEJ0 ? 1 : 0;
+  q.hej_m = (s->green >= FLUPS_HEJ2 && s->green <= FLUPS_HEJ10) ? s->green / 2 : 1;
+  q.eps = s->eps;
+  q.hmax = std::fmax(s->h[0], std::fmax(s->h[1], s->h[2]));
+  gauss_legendre(GL_N, q.gl_x, q.gl_w);
+  return q;
+}
+
+// FP64 samples G(k_s, r_u) of the stored spectrum's kernel, x fastest over the Green extents.
+cudaError_t sample_green(const flups_solver_s* s, const GreenSampleParams& q, double* g64, cudaStream_t st) {
+  return (s->green == FLUPS_LGF2) ? launch_lgf(g64, q.gext, q.h, st) : launch_green_sample(g64, q, st);
 }
 
 int setup_green_compute(flups_solver_s* s, cudaStream_t st) {
@@ -453,26 +494,12 @@ int setup_green_compute(flups_solver_s* s, cudaStream_t st) {
     return FLUPS_OK;
   }
   // stored spectrum: sample G(k_s, r_u) in FP64, DCT-I along each unbounded-like direction
-  GreenSampleParams q{};
+  GreenSampleParams q = green_params(s);
   long long n = 1;
-  for (int d = 0; d < 3; ++d) {
-    const DirPlan& dp = s->dir[d];
-    q.gext[d] = dp.gext;
-    q.unb[d] = dp.unb;
-    q.h[d] = dp.h;
-    q.wscale[d] = dp.wscale;
-    q.wshift[d] = dp.wshift;
-    n *= dp.gext;
-  }
-  q.du = du;
-  q.kernel = s->green == FLUPS_HEJ0 ? 1 : 0;
-  q.hej_m = (s->green >= FLUPS_HEJ2 && s->green <= FLUPS_HEJ10) ? s->green / 2 : 1;
-  q.eps = s->eps;
-  q.hmax = std::fmax(s->h[0], std::fmax(s->h[1], s->h[2]));
-  gauss_legendre(GL_N, q.gl_x, q.gl_w);
+  for (int d = 0; d < 3; ++d) n *= q.gext[d];
   double* g64 = nullptr;
   CK(cudaMallocAsync(&g64, n * sizeof(double), st));
-  cudaError_t e = (s->green == FLUPS_LGF2) ? launch_lgf(g64, q.gext, q.h, st) : launch_green_sample(g64, q, st);
+  cudaError_t e = sample_green(s, q, g64, st);
   if (e) { cudaFreeAsync(g64, st); return cuda_fail(e, "green sample"); }
   double vol = 1.0;
   for (int d = 0; d < 3; ++d) {
@@ -667,6 +694,11 @@ int build_plan(flups_solver_s* s) {
   return FLUPS_OK;
 }
 
+// A caller-provided workspace ends with a 256-byte block whose first int is the device status
+// word of the solve that uses it (zeroed at the start of the solve, set by a bounded wait that
+// gives up), so that concurrent solves of one plan report their device status separately.
+constexpr size_t kStatusBlock = 256;
+
 // Bytes of workspace array i (1: after d1, 2: after d2), padded rows, rounded to 256.
 size_t ws_array_bytes(const flups_solver_s* s, int i) {
   return (((size_t)s->pitch[i] * s->dims[i][1] * s->dims[i][2] * s->topo.ncomp * (s->cplx[i] ? 2 : 1) *
@@ -858,8 +890,7 @@ int build_passes(flups_solver_s* s, cudaStream_t st) {
       // register-chained fused column kernel: stage the tile's Green slice in shared memory
       // (cp.async at kernel start) when that keeps the kernel's CTAs per SM
       const size_t gbytes = (size_t)L.p.W * (dp.P / 2 + 1) * esize(prec);
-      const int threads = L.nthr;
-      const int minb = std::max(1, (prec == FLUPS_F32 ? 1024 : 512) / threads);
+      const int minb = ct_min_blocks(L.p, L.nthr, prec);
       if ((L.smem + gbytes + 128 + 1024) * minb <= 228 * 1024) {
         L.smem += gbytes + 128;  // + alignment of the slice to 128 bytes
         L.p.gpre = 1;
@@ -916,8 +947,27 @@ int build_passes(flups_solver_s* s, cudaStream_t st) {
   return FLUPS_OK;
 }
 
-std::once_flag g_limits_once;
-cudaError_t g_limits_err = cudaSuccess;
+// Dynamic shared-memory limits of the pass and curl kernels: a per-device attribute, so it is set
+// once for every device the library is used on, with that device current.
+constexpr int kMaxDevices = 64;
+std::mutex g_limits_mu;
+bool g_limits_done[kMaxDevices] = {};
+cudaError_t g_limits_err[kMaxDevices] = {};
+
+int ensure_smem_limits() {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return FLUPS_EINVAL;
+  std::lock_guard<std::mutex> lk(g_limits_mu);
+  if (!g_limits_done[dev]) {
+    cudaError_t e = set_pass_smem_limits();
+    if (e == cudaSuccess) e = set_curl_smem_limits();
+    g_limits_err[dev] = e;
+    g_limits_done[dev] = true;
+  }
+  if (g_limits_err[dev] != cudaSuccess) return cuda_fail(g_limits_err[dev], "smem limits");
+  return FLUPS_OK;
+}
 
 }  // namespace
 
@@ -937,6 +987,7 @@ const char* flups_strerror(int status) {
     case FLUPS_ECUDA: return "CUDA error";
     case FLUPS_EGREEN: return "Green kernel not available for these boundary conditions";
     case FLUPS_ESTATE: return "call out of order";
+    case FLUPS_EDEVICE: return "a kernel's bounded wait gave up: the result is not valid";
   }
   return "unknown status";
 }
@@ -1051,11 +1102,10 @@ int flups_setup(flups_solver s, void* stream, size_t* workspace_bytes) {
     if (workspace_bytes) *workspace_bytes = s->ws_bytes;
     return FLUPS_OK;
   }
-  std::call_once(g_limits_once, [] {
-    g_limits_err = set_pass_smem_limits();
-    if (g_limits_err == cudaSuccess) g_limits_err = set_curl_smem_limits();
-  });
-  if (g_limits_err) return cuda_fail(g_limits_err, "smem limits");
+  {
+    const int rc = ensure_smem_limits();
+    if (rc) return rc;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const int prec = s->topo.prec, nc = s->topo.ncomp;
   const size_t es = esize(prec);
@@ -1073,7 +1123,7 @@ int flups_setup(flups_solver s, void* stream, size_t* workspace_bytes) {
   }
   size_t wbytes[3] = {0, 0, 0};
   for (int i = 1; i <= 2; ++i) wbytes[i] = ws_array_bytes(s, i);
-  s->ws_need = wbytes[1] + wbytes[2];
+  s->ws_need = wbytes[1] + wbytes[2] + kStatusBlock;
   if (!s->shared) {
     for (int i = 1; i <= 2; ++i) {
       void** buf = i == 1 ? &s->W1 : &s->W2;
@@ -1110,14 +1160,19 @@ static int solve_impl(flups_solver s, void* phi, const void* rhs, void* ws, void
   cudaStream_t st = (cudaStream_t)stream;
   const int prec = s->topo.prec;
   void* W[3] = {nullptr, s->W1, s->W2};
+  int* status = s->errflag;
   if (ws) {
     const size_t w1 = ws_array_bytes(s, 1);
     W[1] = ws;
     W[2] = (char*)ws + w1;
+    status = (int*)((char*)ws + s->ws_need - kStatusBlock);
+    CK(cudaMemsetAsync(status, 0, sizeof(int), st));
   }
   for (Launch& L : s->passes) {
     Launch Lw = L;
     PassParams& p = Lw.p;
+    p.errflag = status;
+    p.dbg_wait = s->dbg_wait;
     if (L.in_buf) p.in = W[L.in_buf];
     if (L.out_buf) p.out = W[L.out_buf];
     if (L.user_in) p.in = rhs;
@@ -1158,6 +1213,7 @@ int flups_solver_memory(flups_solver s, size_t* resident, size_t* transient, siz
     tr += gn * sizeof(double) + (size_t)8 * 2 * gmax * sizeof(double);
   }
   for (int i = 1; i <= 2; ++i) ws += ws_array_bytes(s, i);
+  ws += kStatusBlock;
   if (resident) *resident = res;
   if (transient) *transient = tr;
   if (workspace) *workspace = ws;
@@ -1168,6 +1224,51 @@ int flups_workspace_size(flups_solver s, size_t* bytes) {
   if (!s || !bytes) return FLUPS_EINVAL;
   if (!s->ready) return FLUPS_ESTATE;
   *bytes = s->ws_need;
+  return FLUPS_OK;
+}
+
+int flups_workspace_status(flups_solver s, size_t* offset) {
+  if (!s || !offset) return FLUPS_EINVAL;
+  if (!s->ready) return FLUPS_ESTATE;
+  *offset = s->ws_need - kStatusBlock;
+  return FLUPS_OK;
+}
+
+int flups_debug_green(flups_solver s, double* samples, double* spectrum, long long n) {
+  if (!s || !samples || !spectrum) return FLUPS_EINVAL;
+  if (!s->ready) return FLUPS_ESTATE;
+  int du = 0;
+  for (int d = 0; d < 3; ++d) du += s->dir[d].unb;
+  if (du == 0 || !s->green_dev) return FLUPS_ESTATE;  // closed form: no stored spectrum
+  GreenSampleParams q = green_params(s);
+  const long long cnt = (long long)q.gext[0] * q.gext[1] * q.gext[2];
+  if (n != cnt) return FLUPS_EINVAL;
+  double* g64 = nullptr;
+  CK(cudaMalloc(&g64, cnt * sizeof(double)));
+  cudaError_t e = sample_green(s, q, g64, nullptr);
+  if (!e) e = cudaMemcpy(samples, g64, cnt * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(g64);
+  if (e) return cuda_fail(e, "flups_debug_green samples");
+  const size_t es = s->topo.prec == FLUPS_F32 ? 4 : 8;
+  const size_t rows = (size_t)q.gext[1] * q.gext[2];
+  std::vector<unsigned char> buf(rows * s->green_pitch * es);
+  CK(cudaMemcpy(buf.data(), s->green_dev, buf.size(), cudaMemcpyDeviceToHost));
+  // element formats: FP32, FP64, or on the double-float path a pair of floats (hi, lo)
+  for (size_t r = 0; r < rows; ++r)
+    for (int x = 0; x < q.gext[0]; ++x) {
+      const size_t i = r * s->green_pitch + x;
+      double v;
+      if (es == 4) v = (double)((const float*)buf.data())[i];
+      else if (s->topo.prec == FLUPS_F64E) v = (double)((const float*)buf.data())[2 * i] + (double)((const float*)buf.data())[2 * i + 1];
+      else v = ((const double*)buf.data())[i];
+      spectrum[r * q.gext[0] + x] = v;
+    }
+  return FLUPS_OK;
+}
+
+int flups_debug_wait_limit(flups_solver s, int mask) {
+  if (!s || mask < 0 || mask > 3) return FLUPS_EINVAL;
+  s->dbg_wait = mask;
   return FLUPS_OK;
 }
 
@@ -1191,6 +1292,7 @@ int flups_solve_pass(flups_solver s, int i, void* phi, const void* rhs, void* st
   if (i < 0 || i >= (int)s->passes.size()) return FLUPS_EINVAL;
   const Launch& L = s->passes[i];
   PassParams p = L.p;
+  p.dbg_wait = s->dbg_wait;
   if (L.user_in) p.in = rhs;
   if (L.user_out) p.out = phi;
   cudaError_t e = L.kind >= K_CURL_REAL
@@ -1232,7 +1334,7 @@ int flups_pass_features(flups_solver s, int i, int* flags) {
   if (!s->ready) return FLUPS_ESTATE;
   if (i < 0 || i >= (int)s->passes.size()) return FLUPS_EINVAL;
   const PassParams& p = s->passes[i].p;
-  *flags = (p.ct ? 1 : 0) | (p.gpre ? 2 : 0) | (p.gmap ? 4 : 0) | (p.hz ? 8 : 0);
+  *flags = (p.ct ? 1 : 0) | (p.gpre ? 2 : 0) | (p.gmap ? 4 : 0) | (p.hz ? 8 : 0) | (p.tin_rows ? 16 : 0);
   return FLUPS_OK;
 }
 
@@ -1397,7 +1499,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[FLUPS_NOALLOC_S
 
 namespace {
 
-constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[kMaxDevices] = {};
 
@@ -1442,8 +1543,10 @@ extern "C" int flups_solve_periodic_noalloc(double* phi, const double* rhs, cons
     }
     base = g_noalloc_addr[dev];
   }
-  std::call_once(g_limits_once, [] { g_limits_err = set_pass_smem_limits(); });
-  if (g_limits_err) return cuda_fail(g_limits_err, "smem limits");
+  {
+    const int rc = ensure_smem_limits();
+    if (rc) return rc;
+  }
 
   // plan: x R2C, y C2C, z fused C2C with the closed-form spectral kernel -1/|k|^2
   DirPlan dir[3];

@@ -73,15 +73,40 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0,
       "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
       : "memory");
 }
-// Bounded wait for phase 0 of an mbarrier; a wait that gives up records `code` (and waits once
-// more, again bounded, for the copies in flight).
-__device__ __forceinline__ void mbar_wait_bounded(unsigned long long* bar, int* errflag, int code) {
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Time limits of a bounded mbarrier wait: the copies it waits for take microseconds, so a wait
+// that has not completed after kWaitLimitNs is declared failed; the kernel then waits at most
+// kDrainLimitNs more for the copies still in flight (so that no copy writes into the shared memory
+// of a CTA that has exited) and skips its global stores.  Once a failure has been recorded, later
+// waits are given kGraceNs only instead of the full limit, so that a solve whose copies never
+// arrive ends quickly.
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s
+constexpr unsigned long long kGraceNs = 1000000ull;          // 1 ms
+constexpr unsigned long long kDrainLimitNs = 100000000ull;   // 0.1 s
+// Bounded wait for phase 0 of an mbarrier.  Returns true when the copies completed within the
+// limit; otherwise records `code` in *errflag (when non-null and still 0: the first code recorded
+// is kept), drains as above and returns false (the tile's data are then not valid).  force_fail
+// (a test hook) makes the first limit zero: the wait gives up at once and only the drain waits for
+// the copies, which do complete.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, int* errflag, int code,
+                                                  bool force_fail = false) {
+  if (!force_fail && mbar_try_wait(bar, 0)) return true;
   bool done = false;
-  for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(bar, 0);
-  if (!done) {
-    if (errflag) atomicExch(errflag, code);
-    for (int it = 0; it < (1 << 22) && !done; ++it) done = mbar_try_wait(bar, 0);
-  }
+  unsigned long long limit = kWaitLimitNs;
+  if (force_fail) limit = 0;
+  else if (errflag && *(volatile int*)errflag != 0) limit = kGraceNs;
+  const unsigned long long t0 = global_ns();
+  while (!done && global_ns() - t0 < limit) done = mbar_try_wait(bar, 0);
+  if (done) return true;
+  if (errflag) atomicCAS(errflag, 0, code);
+  const unsigned long long t1 = global_ns();
+  while (!done && global_ns() - t1 < kDrainLimitNs) done = mbar_try_wait(bar, 0);
+  return false;
 }
 // 3D tile load of the box at coordinates (c0, c1, c2) of the tensor map into shared memory
 __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int c0, int c1, int c2,
@@ -99,20 +124,20 @@ template <> __device__ __forceinline__ dfloat ldg_r<dfloat>(const dfloat* p) {
   return dfloat(q.x, q.y);
 }
 
-template <typename T> __device__ __forceinline__ cpx<T> mk(T re, T im) { cpx<T> c; c.x = re; c.y = im; return c; }
-template <typename T> __device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
-template <typename T> __device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
-template <typename T> __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+template <typename T> __host__ __device__ __forceinline__ cpx<T> mk(T re, T im) { cpx<T> c; c.x = re; c.y = im; return c; }
+template <typename T> __host__ __device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __host__ __device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __host__ __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
   return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 // a * conj(b)
-template <typename T> __device__ __forceinline__ cpx<T> cmulc(cpx<T> a, cpx<T> b) {
+template <typename T> __host__ __device__ __forceinline__ cpx<T> cmulc(cpx<T> a, cpx<T> b) {
   return mk<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
-template <typename T> __device__ __forceinline__ cpx<T> cconj(cpx<T> a) { return mk<T>(a.x, -a.y); }
-template <typename T> __device__ __forceinline__ cpx<T> cscale(cpx<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+template <typename T> __host__ __device__ __forceinline__ cpx<T> cconj(cpx<T> a) { return mk<T>(a.x, -a.y); }
+template <typename T> __host__ __device__ __forceinline__ cpx<T> cscale(cpx<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
 // multiply by -i (forward) or +i (inverse)
-template <typename T, bool INV> __device__ __forceinline__ cpx<T> mul_mi(cpx<T> a) {
+template <typename T, bool INV> __host__ __device__ __forceinline__ cpx<T> mul_mi(cpx<T> a) {
   return INV ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
 }
 
@@ -120,16 +145,16 @@ template <typename T, bool INV> __device__ __forceinline__ cpx<T> mul_mi(cpx<T> 
 // Register DFTs of radix 2, 3, 4, 8, 16 (forward: exp(-2 pi i q r / R)).
 // The constants are the exact values cos(pi/4), cos(pi/8), sin(pi/8), sqrt(3)/2.
 // ---------------------------------------------------------------------------
-template <typename T, bool INV> __device__ __forceinline__ void dft2(cpx<T>& a, cpx<T>& b) {
+template <typename T, bool INV> __host__ __device__ __forceinline__ void dft2(cpx<T>& a, cpx<T>& b) {
   cpx<T> t = a; a = cadd<T>(t, b); b = csub<T>(t, b);
 }
 
-template <typename T, bool INV> __device__ __forceinline__ void dft4(cpx<T>& a, cpx<T>& b, cpx<T>& c, cpx<T>& d) {
+template <typename T, bool INV> __host__ __device__ __forceinline__ void dft4(cpx<T>& a, cpx<T>& b, cpx<T>& c, cpx<T>& d) {
   cpx<T> t0 = cadd<T>(a, c), t1 = csub<T>(a, c), t2 = cadd<T>(b, d), t3 = mul_mi<T, INV>(csub<T>(b, d));
   a = cadd<T>(t0, t2); c = csub<T>(t0, t2); b = cadd<T>(t1, t3); d = csub<T>(t1, t3);
 }
 
-template <typename T, bool INV> __device__ __forceinline__ void dft3(cpx<T>& a, cpx<T>& b, cpx<T>& c) {
+template <typename T, bool INV> __host__ __device__ __forceinline__ void dft3(cpx<T>& a, cpx<T>& b, cpx<T>& c) {
   const T s3 = (T)0.86602540378443864676372317075294;
   cpx<T> t1 = cadd<T>(b, c);
   cpx<T> t2 = mk<T>(a.x - (T)0.5 * t1.x, a.y - (T)0.5 * t1.y);
@@ -138,17 +163,17 @@ template <typename T, bool INV> __device__ __forceinline__ void dft3(cpx<T>& a, 
 }
 
 // rotate by W8^1 = (1 - i)/sqrt2 (forward) or its conjugate
-template <typename T, bool INV> __device__ __forceinline__ cpx<T> rot8_1(cpx<T> a) {
+template <typename T, bool INV> __host__ __device__ __forceinline__ cpx<T> rot8_1(cpx<T> a) {
   const T r = (T)0.70710678118654752440084436210485;
   return INV ? mk<T>(r * (a.x - a.y), r * (a.x + a.y)) : mk<T>(r * (a.x + a.y), r * (a.y - a.x));
 }
 // rotate by W8^3 = (-1 - i)/sqrt2 (forward) or its conjugate
-template <typename T, bool INV> __device__ __forceinline__ cpx<T> rot8_3(cpx<T> a) {
+template <typename T, bool INV> __host__ __device__ __forceinline__ cpx<T> rot8_3(cpx<T> a) {
   const T r = (T)0.70710678118654752440084436210485;
   return INV ? mk<T>(-r * (a.x + a.y), r * (a.x - a.y)) : mk<T>(r * (a.y - a.x), -r * (a.x + a.y));
 }
 
-template <typename T, bool INV> __device__ __forceinline__ void dft8(cpx<T>* v) {
+template <typename T, bool INV> __host__ __device__ __forceinline__ void dft8(cpx<T>* v) {
   // radix-2 DIT on top of two radix-4 DFTs
   cpx<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
   cpx<T> o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
@@ -163,7 +188,7 @@ template <typename T, bool INV> __device__ __forceinline__ void dft8(cpx<T>* v) 
   v[3] = cadd<T>(e3, o3); v[7] = csub<T>(e3, o3);
 }
 
-template <typename T, bool INV> __device__ __forceinline__ cpx<T> tw16(cpx<T> a, int m) {
+template <typename T, bool INV> __host__ __device__ __forceinline__ cpx<T> tw16(cpx<T> a, int m) {
   // multiply by W16^m, m in [0, 9]
   const T c1 = (T)0.92387953251128675612818318939679;   // cos(pi/8)
   const T s1 = (T)0.38268343236508977172845998403040;   // sin(pi/8)
@@ -183,7 +208,7 @@ template <typename T, bool INV> __device__ __forceinline__ cpx<T> tw16(cpx<T> a,
   return mk<T>(a.x * c + a.y * s, a.y * c - a.x * s);
 }
 
-template <typename T, bool INV> __device__ __forceinline__ void dft16(cpx<T>* v) {
+template <typename T, bool INV> __host__ __device__ __forceinline__ void dft16(cpx<T>* v) {
   // 4 x 4: columns n2 = 0..3 hold x[4 n1 + n2]
 #pragma unroll
   for (int n2 = 0; n2 < 4; ++n2) dft4<T, INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
@@ -209,12 +234,91 @@ template <typename T, bool INV> __device__ __forceinline__ void dft16(cpx<T>* v)
     for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
 }
 
-template <typename T, int R, bool INV> __device__ __forceinline__ void dftR(cpx<T>* v) {
+// cos(pi m / 16) for any integer m, from the exact first-octant values
+// cos(0, pi/16, pi/8, 3pi/16, pi/4) and sin(3pi/16, pi/8, pi/16) (= cos of 5pi/16, 3pi/8, 7pi/16).
+__host__ __device__ constexpr double cos_pi16_octant(int m) {  // 0 <= m <= 8
+  return m == 0 ? 1.0
+       : m == 1 ? 0.980785280403230449126182236134239
+       : m == 2 ? 0.9238795325112867561281831893967883
+       : m == 3 ? 0.8314696123025452370787883776179058
+       : m == 4 ? 0.707106781186547524400844362104849
+       : m == 5 ? 0.5555702330196022247428308139485329
+       : m == 6 ? 0.3826834323650897717284599840303989
+       : m == 7 ? 0.1950903220161282678482848684770222
+       : 0.0;
+}
+__host__ __device__ constexpr double cos_pi16(int m) {
+  int r = ((m % 32) + 32) % 32;  // period 32
+  if (r > 16) r = 32 - r;        // even
+  return r > 8 ? -cos_pi16_octant(16 - r) : cos_pi16_octant(r);
+}
+
+// multiply by W32^M = exp(-2 pi i M / 32) (forward) or its conjugate, M a compile-time constant
+template <typename T, bool INV, int M> __host__ __device__ __forceinline__ cpx<T> tw32(cpx<T> a) {
+  constexpr int m = M & 31;
+  if constexpr (m == 0) {
+    return a;
+  } else if constexpr (m == 8) {
+    return mul_mi<T, INV>(a);
+  } else if constexpr (m == 16) {
+    return mk<T>(-a.x, -a.y);
+  } else if constexpr (m == 24) {
+    return mul_mi<T, !INV>(a);
+  } else {
+    constexpr double c = cos_pi16(m), sn = cos_pi16(8 - m);  // W32^m = c - i sn
+    const T cc = (T)c, s = INV ? (T)(-sn) : (T)sn;
+    return mk<T>(a.x * cc + a.y * s, a.y * cc - a.x * s);
+  }
+}
+
+// DFT-4 of (a, b, 0, 0): the upper half of the inputs is zero padding
+template <typename T, bool INV> __host__ __device__ __forceinline__ void dft4_half(cpx<T>& a, cpx<T>& b, cpx<T>& c,
+                                                                                  cpx<T>& d) {
+  const cpx<T> t3 = mul_mi<T, INV>(b);
+  c = csub<T>(a, b);
+  d = csub<T>(a, t3);
+  const cpx<T> a0 = a;
+  a = cadd<T>(a0, b);
+  b = cadd<T>(a0, t3);
+}
+
+template <typename T, bool INV, int K1, int N2> __host__ __device__ __forceinline__ void dft32_twiddle(cpx<T>* v) {
+  if constexpr (N2 < 8) {
+    v[8 * K1 + N2] = tw32<T, INV, N2 * K1>(v[8 * K1 + N2]);
+    dft32_twiddle<T, INV, K1, N2 + 1>(v);
+  }
+}
+
+// DFT-32 in registers as 4 x 8: inputs x[8 n1 + n2]; a DFT-4 over n1 for every n2 (ZH: the
+// inputs 16..31 are zero padding), twiddles W32^(n2 k1), a DFT-8 over n2 for every k1, which
+// leaves X[k1 + 4 k2] in v[8 k1 + k2]; the index is then transposed to natural order.
+template <typename T, bool INV, bool ZH = false> __host__ __device__ __forceinline__ void dft32(cpx<T>* v) {
+#pragma unroll
+  for (int n2 = 0; n2 < 8; ++n2) {
+    if constexpr (ZH) dft4_half<T, INV>(v[n2], v[8 + n2], v[16 + n2], v[24 + n2]);
+    else dft4<T, INV>(v[n2], v[8 + n2], v[16 + n2], v[24 + n2]);
+  }
+  dft32_twiddle<T, INV, 1, 1>(v);
+  dft32_twiddle<T, INV, 2, 1>(v);
+  dft32_twiddle<T, INV, 3, 1>(v);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft8<T, INV>(&v[8 * k1]);
+  cpx<T> t[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) t[i] = v[i];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) v[k1 + 4 * k2] = t[8 * k1 + k2];
+}
+
+template <typename T, int R, bool INV> __host__ __device__ __forceinline__ void dftR(cpx<T>* v) {
   if constexpr (R == 2) dft2<T, INV>(v[0], v[1]);
   else if constexpr (R == 3) dft3<T, INV>(v[0], v[1], v[2]);
   else if constexpr (R == 4) dft4<T, INV>(v[0], v[1], v[2], v[3]);
   else if constexpr (R == 8) dft8<T, INV>(v);
   else if constexpr (R == 16) dft16<T, INV>(v);
+  else if constexpr (R == 32) dft32<T, INV>(v);
 }
 
 // ---------------------------------------------------------------------------
@@ -361,6 +465,32 @@ __host__ __device__ constexpr int ct_rad_rev(int P, int s) { return ct_rad(P, ct
 __host__ __device__ constexpr int ct_ns_rev(int P, int s) {
   int ns = 1;
   for (int i = 0; i < s; ++i) ns *= ct_rad_rev(P, i);
+  return ns;
+}
+
+// Plans of the column kernels, parameterised by the elements a thread holds in a stage: EPT = 16
+// is the plan above; EPT = 32 takes radix-32 stages (1024 = 32 x 32, 512 = 32 x 16, 2048 =
+// 32 x 8 x 8), one twiddled stage fewer per transform and half the threads per tile.
+__host__ __device__ constexpr int ct_radix_e(int rem, int ept) {
+  return ept == 32 ? (rem == 64 ? 8 : (rem >= 32 ? 32 : rem)) : ct_radix(rem);
+}
+__host__ __device__ constexpr int ct_nstages_e(int P, int ept) {
+  int n = 0, ns = 1;
+  while (ns < P) { ns *= ct_radix_e(P / ns, ept); ++n; }
+  return n;
+}
+__host__ __device__ constexpr int ct_ns_e(int P, int s, int ept) {
+  int ns = 1;
+  for (int i = 0; i < s; ++i) ns *= ct_radix_e(P / ns, ept);
+  return ns;
+}
+__host__ __device__ constexpr int ct_rad_e(int P, int s, int ept) { return ct_radix_e(P / ct_ns_e(P, s, ept), ept); }
+__host__ __device__ constexpr int ct_rad_rev_e(int P, int s, int ept) {
+  return ct_rad_e(P, ct_nstages_e(P, ept) - 1 - s, ept);
+}
+__host__ __device__ constexpr int ct_ns_rev_e(int P, int s, int ept) {
+  int ns = 1;
+  for (int i = 0; i < s; ++i) ns *= ct_rad_rev_e(P, i, ept);
   return ns;
 }
 

@@ -33,6 +33,13 @@ template <typename T, int PC, int WC> struct KBounds {
   static constexpr int minb = PC ? ((sizeof(T) == 4 ? 1024 : 512) / threads > 0 ? (sizeof(T) == 4 ? 1024 : 512) / threads : 1) : 1;
 };
 
+// Column kernels: EPT elements per thread and stage (16, or 32 with radix-32 stages), so
+// P W / EPT threads; with EPT = 32 a thread may use up to 128 registers (2 CTAs of 256 threads per SM).
+template <typename T, int PC, int WC, int EPT> struct ColBounds {
+  static constexpr int threads = PC * WC / EPT;
+  static constexpr int minb = EPT == 32 ? (512 / threads > 0 ? 512 / threads : 1) : KBounds<T, PC, WC>::minb;
+};
+
 template <typename T, int PC, int WC>
 struct Tile {
   static constexpr bool CT = PC > 0;
@@ -500,7 +507,8 @@ __device__ __forceinline__ void xstage(cpx<T>* S, cpx<T>* v, const cpx<T>* __res
   constexpr int LS = CR::LS, LG = CR::LG;
   constexpr int nbf = P / R;
   constexpr int NB = (nbf * W) / NT;
-  static_assert(NB * R == 16, "16 elements per thread");
+  constexpr int EPT = P * W / NT;
+  static_assert(NB * R == EPT && (EPT == 16 || EPT == 32), "16 or 32 elements per thread");
   static_assert(CR::G == 1 || (nbf >= CR::G && R >= CR::G && (Ns == 1 || Ns >= CR::G)), "row permutation fields");
   constexpr int tstep = (2 * P) / (Ns * R);
   if constexpr (SRC != XS_REGS) {
@@ -544,7 +552,8 @@ __device__ __forceinline__ void xstage(cpx<T>* S, cpx<T>* v, const cpx<T>* __res
         v[b * R + r] = INV ? cmulc<T>(v[b * R + r], w) : cmul<T>(v[b * R + r], w);
       }
     }
-    dftR<T, R, INV>(&v[b * R]);
+    if constexpr (ZIN && R == 32) dft32<T, INV, true>(&v[b * R]);   // inputs 16..31 are zero padding
+    else dftR<T, R, INV>(&v[b * R]);
   }
   if constexpr (DST != XS_REGS) {
 #pragma unroll
@@ -580,17 +589,18 @@ __device__ __forceinline__ void xstage(cpx<T>* S, cpx<T>* v, const cpx<T>* __res
   }
 }
 
-template <typename T, int P, int W, bool INV, bool REV, int s, int SRC0, int DSTL, bool ZIN = false, bool ZOUT = false>
+template <typename T, int P, int W, bool INV, bool REV, int s, int SRC0, int DSTL, bool ZIN = false, bool ZOUT = false,
+          int EPT = 16>
 __device__ __forceinline__ void xstages(cpx<T>* S, cpx<T>* v, const cpx<T>* __restrict__ tw, int tid,
                                         const ColIO<T>& io) {
-  constexpr int NS = ct_nstages(P);
+  constexpr int NS = ct_nstages_e(P, EPT);
   if constexpr (s < NS) {
-    constexpr int R = REV ? ct_rad_rev(P, s) : ct_rad(P, s);
-    constexpr int Ns = REV ? ct_ns_rev(P, s) : ct_ns(P, s);
+    constexpr int R = REV ? ct_rad_rev_e(P, s, EPT) : ct_rad_e(P, s, EPT);
+    constexpr int Ns = REV ? ct_ns_rev_e(P, s, EPT) : ct_ns_e(P, s, EPT);
     constexpr int SRC = s == 0 ? SRC0 : (int)XS_SMEM;
     constexpr int DST = s == NS - 1 ? DSTL : (int)XS_SMEM;
-    xstage<T, P, W, P * W / 16, R, Ns, INV, SRC, DST, ZIN && s == 0, ZOUT && s == NS - 1>(S, v, tw, tid, io);
-    xstages<T, P, W, INV, REV, s + 1, SRC0, DSTL, ZIN, ZOUT>(S, v, tw, tid, io);
+    xstage<T, P, W, P * W / EPT, R, Ns, INV, SRC, DST, ZIN && s == 0, ZOUT && s == NS - 1>(S, v, tw, tid, io);
+    xstages<T, P, W, INV, REV, s + 1, SRC0, DSTL, ZIN, ZOUT, EPT>(S, v, tw, tid, io);
   }
 }
 
@@ -643,56 +653,56 @@ __device__ __forceinline__ void tile_tma_issue(const PassParams& p, cpx<T>* S, u
   }
 }
 
-template <typename T, int PC, int WC, bool HZ>
-__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb)
+template <typename T, int PC, int WC, bool HZ, int EPT = 16>
+__global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<T, PC, WC, EPT>::minb)
     k_fwd_c2c_col(const __grid_constant__ PassParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   unsigned char* base = col_base(smraw);
   unsigned long long* mbar_in = reinterpret_cast<unsigned long long*>(base - 128);
   cpx<T>* S = reinterpret_cast<cpx<T>*>(base);
-  cpx<T> v[16];
+  cpx<T> v[EPT];
   const int tid = threadIdx.x;
-  const ColIO<T> io = col_io<T>(p, WC, p.n_use, PC, -1, blockIdx.y);
+  ColIO<T> io = col_io<T>(p, WC, p.n_use, PC, -1, blockIdx.y);
   const cpx<T>* tw = (const cpx<T>*)p.tw;
   if (p.tin_rows) {
     if (tid == 0) mbar_init(mbar_in, 1);
     __syncthreads();
     if (tid == 0) tile_tma_issue<T, WC>(p, S, mbar_in, blockIdx.y);
-    mbar_wait_bounded(mbar_in, p.errflag, 2);
-    xstages<T, PC, WC, false, false, 0, XS_NAT, XS_GLOBAL, HZ, false>(S, v, tw, tid, io);
+    if (!mbar_wait_bounded(mbar_in, p.errflag, 2, p.dbg_wait & 2)) io.npen = 0;  // no stores of a partial tile
+    xstages<T, PC, WC, false, false, 0, XS_NAT, XS_GLOBAL, HZ, false, EPT>(S, v, tw, tid, io);
   } else {
-    xstages<T, PC, WC, false, false, 0, XS_GLOBAL, XS_GLOBAL, HZ, false>(S, v, tw, tid, io);
+    xstages<T, PC, WC, false, false, 0, XS_GLOBAL, XS_GLOBAL, HZ, false, EPT>(S, v, tw, tid, io);
   }
 }
 
-template <typename T, int PC, int WC, bool HZ>
-__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb)
+template <typename T, int PC, int WC, bool HZ, int EPT = 16>
+__global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<T, PC, WC, EPT>::minb)
     k_inv_c2c_col(const __grid_constant__ PassParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   unsigned char* base = col_base(smraw);
   unsigned long long* mbar_in = reinterpret_cast<unsigned long long*>(base - 128);
   cpx<T>* S = reinterpret_cast<cpx<T>*>(base);
-  cpx<T> v[16];
+  cpx<T> v[EPT];
   const int tid = threadIdx.x;
   const int dup = (p.type == T_PER && p.center == C_NODE && p.n_data > p.N) ? p.N : -1;
-  const ColIO<T> io = col_io<T>(p, WC, PC, p.n_data, dup, blockIdx.y);
+  ColIO<T> io = col_io<T>(p, WC, PC, p.n_data, dup, blockIdx.y);
   const cpx<T>* tw = (const cpx<T>*)p.tw;
   if (p.tin_rows) {
     if (tid == 0) mbar_init(mbar_in, 1);
     __syncthreads();
     if (tid == 0) tile_tma_issue<T, WC>(p, S, mbar_in, blockIdx.y);
-    mbar_wait_bounded(mbar_in, p.errflag, 2);
-    xstages<T, PC, WC, true, false, 0, XS_NAT, XS_GLOBAL, false, HZ>(S, v, tw, tid, io);
+    if (!mbar_wait_bounded(mbar_in, p.errflag, 2, p.dbg_wait & 2)) io.npen = 0;
+    xstages<T, PC, WC, true, false, 0, XS_NAT, XS_GLOBAL, false, HZ, EPT>(S, v, tw, tid, io);
   } else {
-    xstages<T, PC, WC, true, false, 0, XS_GLOBAL, XS_GLOBAL, false, HZ>(S, v, tw, tid, io);
+    xstages<T, PC, WC, true, false, 0, XS_GLOBAL, XS_GLOBAL, false, HZ, EPT>(S, v, tw, tid, io);
   }
 }
 
-template <typename T, int PC, int WC, bool HZ>
-__global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb)
+template <typename T, int PC, int WC, bool HZ, int EPT = 16>
+__global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<T, PC, WC, EPT>::minb)
     k_fused_c2c_col(const __grid_constant__ PassParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  constexpr int P = PC, W = WC, NT = PC * WC / 16;
+  constexpr int P = PC, W = WC, NT = PC * WC / EPT;
   unsigned char* base = col_base(smraw);
   unsigned long long* mbar_in = reinterpret_cast<unsigned long long*>(base - 128);
   unsigned long long* mbar_g = mbar_in + 1;
@@ -750,22 +760,22 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     for (int lane = tid; lane < W; lane += NT) pencil_green_base<T>(p, q0 + lane, o, &goff[lane], &k2p[lane]);
   }
   const int dup = (p.type == T_PER && p.center == C_NODE && p.n_data > p.N) ? p.N : -1;
-  const ColIO<T> io = col_io<T>(p, W, p.n_use, p.n_data, dup, o);
+  ColIO<T> io = col_io<T>(p, W, p.n_use, p.n_data, dup, o);
   const cpx<T>* tw = (const cpx<T>*)p.tw;
-  cpx<T> v[16];
+  cpx<T> v[EPT];
   // forward: HBM (or the TMA tile) -> ... -> registers (the first stage's barrier also publishes goff/k2p)
   if (p.tin_rows) {
-    mbar_wait_bounded(mbar_in, p.errflag, 2);
-    xstages<T, P, W, false, false, 0, XS_NAT, XS_REGS, HZ, false>(S, v, tw, tid, io);
+    if (!mbar_wait_bounded(mbar_in, p.errflag, 2, p.dbg_wait & 2)) io.npen = 0;
+    xstages<T, P, W, false, false, 0, XS_NAT, XS_REGS, HZ, false, EPT>(S, v, tw, tid, io);
   } else {
-    xstages<T, P, W, false, false, 0, XS_GLOBAL, XS_REGS, HZ, false>(S, v, tw, tid, io);
+    xstages<T, P, W, false, false, 0, XS_GLOBAL, XS_REGS, HZ, false, EPT>(S, v, tw, tid, io);
   }
-  // u^ = G^ f^ on the 16 elements this thread holds: indices j + r P/RL
-  constexpr int RL = ct_rad(P, ct_nstages(P) - 1);
-  constexpr int NB = 16 / RL;
+  // u^ = G^ f^ on the EPT elements this thread holds: indices j + r P/RL
+  constexpr int RL = ct_rad_e(P, ct_nstages_e(P, EPT) - 1, EPT);
+  constexpr int NB = EPT / RL;
   if (p.gpre) {
     if (tma_g) {
-      mbar_wait_bounded(mbar_g, p.errflag, 1);
+      if (!mbar_wait_bounded(mbar_g, p.errflag, 1, p.dbg_wait & 1)) io.npen = 0;
     } else {
       cp_async_wait_all();
       __syncthreads();
@@ -796,15 +806,28 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     }
   }
   // inverse, radices in reverse order: registers -> ... -> HBM
-  xstages<T, P, W, true, true, 0, XS_REGS, XS_GLOBAL, false, HZ>(S, v, tw, tid, io);
+  xstages<T, P, W, true, true, 0, XS_REGS, XS_GLOBAL, false, HZ, EPT>(S, v, tw, tid, io);
 }
 
 // ---------------------------------------------------------------------------
 // Instantiation helpers: one launcher and one smem-limit setter per <T, PC, WC>.
 // ---------------------------------------------------------------------------
+// Column kernels with radix-32 stages (32 elements per thread) are compiled for FP32 at P = 1024.
+template <typename T, int PC> constexpr bool has_ept32() { return std::is_same<T, float>::value && PC == 1024; }
+
 template <typename T, int PC, int WC, bool HZ>
 cudaError_t launch_kind_hz(int kind, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st) {
   if constexpr (PC > 0) {
+    if constexpr (has_ept32<T, PC>()) {
+      if (p.axis != 0 && p.ept == 32) {
+        switch (kind) {
+          case K_FWD_C2C: k_fwd_c2c_col<T, PC, WC, HZ, 32><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
+          case K_INV_C2C: k_inv_c2c_col<T, PC, WC, HZ, 32><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
+          case K_FUSED_C2C: k_fused_c2c_col<T, PC, WC, HZ, 32><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
+          default: break;
+        }
+      }
+    }
     if (p.axis != 0) {  // column passes of complex data: register-chained kernels
       switch (kind) {
         case K_FWD_C2C: k_fwd_c2c_col<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
@@ -849,6 +872,11 @@ cudaError_t set_limits_hz() {
     if ((e = cudaFuncSetAttribute(k_fwd_c2c_col<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(k_inv_c2c_col<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(k_fused_c2c_col<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if constexpr (has_ept32<T, PC>()) {
+      if ((e = cudaFuncSetAttribute(k_fwd_c2c_col<T, PC, WC, HZ, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+      if ((e = cudaFuncSetAttribute(k_inv_c2c_col<T, PC, WC, HZ, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+      if ((e = cudaFuncSetAttribute(k_fused_c2c_col<T, PC, WC, HZ, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    }
   }
   return cudaFuncSetAttribute(k_fused_c2c<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }

@@ -19,6 +19,8 @@ int ct_tile_width(int P, int prec) {
   return 0;
 }
 
+int ct_col_ept(int P, int prec) { return (prec == 0 && P == 1024) ? 32 : 16; }
+
 cudaError_t set_pass_smem_limits() {
   cudaError_t e = set_limits_kind<float, 0, 0>();
   if (!e) e = set_limits_kind<double, 0, 0>();

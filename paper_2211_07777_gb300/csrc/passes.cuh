@@ -64,6 +64,7 @@ struct PassParams {
   int ndlog;              // log2 of a power of two >= n_data, n_use, n_modes (row-mode index loops)
   int hlog;               // log2 of a power of two >= P/2 + 1
   int ct;                 // 1: compile-time tile engine (P = 2^a, W from ct_tile_width)
+  int ept;                // column passes of that engine: elements per thread and stage (16 or 32)
   int in_f64, out_f64;    // double-float path: the input / output is the caller's FP64 array
   int hz;                 // cell-centred doubled transform: half-zero input, half output kept (ct engine)
   int gpre;               // fused column pass: copy the tile's stored Green slice to shared memory up front
@@ -71,6 +72,7 @@ struct PassParams {
                           // aligned; boxes of gbox rows and of 1 row along the fused axis), else nullptr
   int gbox;               // rows per box of the first tensor map
   int* errflag;           // device word: set to a nonzero code when a bounded wait gives up
+  int dbg_wait;           // test hook: bit (code - 1) set makes the bounded wait of that code give up at once
   // column passes of the compile-time engine: the input tile by TMA (0 rows: loads from registers)
   int tin_rows;           // rows along the axis copied into the tile (P/2 when pruned, else P)
   int tin_box;            // rows per TMA box
@@ -91,6 +93,8 @@ cudaError_t launch_pass(int kind, int prec, const PassParams& p, dim3 grid, int 
 cudaError_t set_pass_smem_limits();
 // compile-time tile engine: lanes per tile for P = 2^a (32 <= P <= 2048), 0 when not compiled
 int ct_tile_width(int P, int prec);
+// compile-time column passes: elements per thread and stage (32: radix-32 stages), 16 otherwise
+int ct_col_ept(int P, int prec);
 cudaError_t launch_ct_f32(int P, int kind, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st);
 cudaError_t launch_ct_f64(int P, int kind, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st);
 cudaError_t set_limits_ct_f32();

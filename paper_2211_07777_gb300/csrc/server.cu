@@ -12,7 +12,10 @@
 // while the serving loop keeps admitting and completing other requests.
 // Idle slots and plans are evicted least recently used first when a new
 // request needs the memory.  Completion times come from a host function
-// enqueued after the result's device-to-host copy.
+// enqueued after the result's device-to-host copy.  Each slot's workspace
+// carries the device status word of the solve that runs in it; it is copied
+// to pinned host memory after the solve, so a kernel whose bounded wait gave
+// up fails exactly the ticket whose result it would have invalidated.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -41,6 +44,7 @@ struct Slot {
   void* d_rhs = nullptr;
   void* d_phi = nullptr;
   void* d_ws = nullptr;
+  int* h_status = nullptr;   // pinned copy of the device status word of the slot's last solve
   cudaGraphExec_t graph = nullptr;
   bool busy = false;
   double last_use = 0;
@@ -51,6 +55,7 @@ struct Plan {
   flups_topo topo = nullptr;
   flups_solver solver = nullptr;
   size_t resident = 0, transient = 0, ws = 0, io = 0;
+  size_t status_off = 0;      // byte offset of the device status word in a slot's workspace
   std::vector<Slot*> slots;
   int inflight = 0;
   double last_use = 0;
@@ -130,6 +135,10 @@ struct flups_server_s {
   std::list<InFlight*> inflight;
   std::deque<Done> done;
   flups_server_stats st{};
+  // pinned host words for the slots' device status (allocated in chunks, never returned before
+  // destroy, so that releasing a slot needs no synchronising cudaFreeHost)
+  std::vector<int*> status_chunks;
+  std::vector<int*> status_free;
 };
 
 namespace {
@@ -156,7 +165,23 @@ void worker_main(flups_server_s* sv, int device) {
   if (st) cudaStreamDestroy(st);
 }
 
+constexpr int kStatusChunk = 1024;
+
+int* take_status_word(flups_server_s* sv) {
+  if (sv->status_free.empty()) {
+    int* chunk = nullptr;
+    if (cudaMallocHost((void**)&chunk, kStatusChunk * sizeof(int)) != cudaSuccess) return nullptr;
+    sv->status_chunks.push_back(chunk);
+    for (int i = 0; i < kStatusChunk; ++i) sv->status_free.push_back(chunk + i);
+  }
+  int* w = sv->status_free.back();
+  sv->status_free.pop_back();
+  *w = 0;
+  return w;
+}
+
 void free_slot(flups_server_s* sv, Plan* p, Slot* s) {
+  if (s->h_status) sv->status_free.push_back(s->h_status);
   if (s->graph) cudaGraphExecDestroy(s->graph);
   if (s->d_rhs) cudaFreeAsync(s->d_rhs, sv->setup_stream);
   if (s->d_phi) cudaFreeAsync(s->d_phi, sv->setup_stream);
@@ -303,7 +328,12 @@ int try_start(flups_server_s* sv, Pending& pd) {
   if (!slot) {
     slot = new (std::nothrow) Slot;
     if (!slot) return FLUPS_ENOMEM;
-    int rc = cu(cudaMallocAsync(&slot->d_rhs, p->io, sv->setup_stream));
+    int rc = flups_workspace_status(p->solver, &p->status_off);
+    if (!rc) {
+      slot->h_status = take_status_word(sv);
+      if (!slot->h_status) rc = FLUPS_ENOMEM;
+    }
+    if (!rc) rc = cu(cudaMallocAsync(&slot->d_rhs, p->io, sv->setup_stream));
     if (!rc) rc = cu(cudaMallocAsync(&slot->d_phi, p->io, sv->setup_stream));
     if (!rc) rc = cu(cudaMallocAsync(&slot->d_ws, p->ws, sv->setup_stream));
     if (!rc) rc = cu(cudaStreamSynchronize(sv->setup_stream));
@@ -338,6 +368,8 @@ int try_start(flups_server_s* sv, Pending& pd) {
   f->t_submit = pd.t_submit;
   int rc = cu(cudaMemcpyAsync(slot->d_rhs, pd.rhs_host, p->io, cudaMemcpyHostToDevice, s));
   if (!rc) rc = cu(cudaGraphLaunch(slot->graph, s));
+  if (!rc) rc = cu(cudaMemcpyAsync(slot->h_status, (const char*)slot->d_ws + p->status_off, sizeof(int),
+                                   cudaMemcpyDeviceToHost, s));
   if (!rc) rc = cu(cudaMemcpyAsync(pd.phi_host, slot->d_phi, p->io, cudaMemcpyDeviceToHost, s));
   if (!rc) rc = cu(cudaLaunchHostFunc(s, on_complete, f));
   if (rc) {
@@ -372,11 +404,18 @@ void reap(flups_server_s* sv) {
   for (auto it = sv->inflight.begin(); it != sv->inflight.end();) {
     InFlight* f = *it;
     if (f->done.load(std::memory_order_acquire)) {
-      sv->done.push_back({f->ticket, f->t_done - f->t_submit, FLUPS_OK});
+      // the status word was copied before the host function ran (same stream)
+      const int code = *(volatile int*)f->slot->h_status;
+      if (code == 0) {
+        sv->done.push_back({f->ticket, f->t_done - f->t_submit, FLUPS_OK});
+        sv->st.completed++;
+      } else {
+        sv->done.push_back({f->ticket, -1.0, FLUPS_EDEVICE});
+        sv->st.failed++;
+      }
       f->slot->busy = false;
       f->slot->last_use = now_s();
       f->plan->inflight--;
-      sv->st.completed++;
       delete f;
       it = sv->inflight.erase(it);
     } else {
@@ -531,6 +570,7 @@ int flups_server_destroy(flups_server sv) {
   for (cudaStream_t s : sv->streams) cudaStreamDestroy(s);
   cudaStreamDestroy(sv->setup_stream);
   cudaStreamDestroy(sv->capture_stream);
+  for (int* c : sv->status_chunks) cudaFreeHost(c);
   delete sv;
   return FLUPS_OK;
 }

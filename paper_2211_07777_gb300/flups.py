@@ -30,7 +30,8 @@ EXPORTED = (
     "flups_setup_shared", "flups_cleanup_async", "flups_workspace_size", "flups_solve_ws", "flups_solver_memory",
     "flups_server_create", "flups_server_submit", "flups_server_poll", "flups_server_wait", "flups_server_pending",
     "flups_server_get_stats", "flups_server_destroy", "flups_solver_check", "flups_pass_features",
-    "flups_solver_share_green", "flups_host_mapped", "flups_solver_order",
+    "flups_solver_share_green", "flups_host_mapped", "flups_solver_order", "flups_workspace_status",
+    "flups_debug_wait_limit", "flups_measure_fma_peak", "flups_debug_green",
 )
 
 
@@ -95,6 +96,10 @@ def lib():
         L.flups_solver_order.argtypes = [vp, ip]
         L.flups_solver_share_green.argtypes = [vp]
         L.flups_pass_features.argtypes = [vp, ctypes.c_int, ip]
+        L.flups_workspace_status.argtypes = [vp, szp]
+        L.flups_debug_wait_limit.argtypes = [vp, ctypes.c_int]
+        L.flups_measure_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
+        L.flups_debug_green.argtypes = [vp, dp, dp, ctypes.c_longlong]
         llp = ctypes.POINTER(ctypes.c_longlong)
         L.flups_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]
         L.flups_server_submit.argtypes = [vp, ctypes.POINTER(Request), vp, vp, llp]
@@ -251,6 +256,35 @@ def flups_workspace_size(solver) -> int:
     return b.value
 
 
+def flups_workspace_status(solver) -> int:
+    """Byte offset, within a workspace, of the device status word of the solve using it."""
+    b = ctypes.c_size_t(0)
+    _check(lib().flups_workspace_status(solver, ctypes.byref(b)), "flups_workspace_status")
+    return b.value
+
+
+def flups_debug_green(solver, n: int):
+    """(FP64 samples, stored spectrum) of the solver's Green's function, n values each (numpy)."""
+    import numpy as np
+    a = np.zeros(n)
+    b = np.zeros(n)
+    _check(lib().flups_debug_green(solver, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(n)), "flups_debug_green")
+    return a, b
+
+
+def flups_debug_wait_limit(solver, mask: int):
+    _check(lib().flups_debug_wait_limit(solver, int(mask)), "flups_debug_wait_limit")
+
+
+def flups_measure_fma_peak(prec, iters):
+    """(TFLOP/s, ms) of the FMA microbenchmark on the current device (prec F32 or F64)."""
+    t, m = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().flups_measure_fma_peak(int(prec), int(iters), ctypes.byref(t), ctypes.byref(m)),
+           "flups_measure_fma_peak")
+    return t.value, m.value
+
+
 def flups_solve_ws(solver, phi, rhs, workspace, stream=None):
     _check(lib().flups_solve_ws(solver, _ptr(phi), _ptr(rhs), _ptr(workspace), _stream(stream)), "flups_solve_ws")
 
@@ -387,8 +421,13 @@ class Solver:
             f = ctypes.c_int(0)
             _check(lib().flups_pass_features(self._s, i, ctypes.byref(f)), "flups_pass_features")
             v = f.value
-            out.append({"ct": bool(v & 1), "staged_green": bool(v & 2), "tma_green": bool(v & 4), "pruned": bool(v & 8)})
+            out.append({"ct": bool(v & 1), "staged_green": bool(v & 2), "tma_green": bool(v & 4), "pruned": bool(v & 8),
+                        "tma_input": bool(v & 16)})
         return out
+
+    def debug_wait_limit(self, mask: int):
+        """Test hook: bounded waits of the codes in mask (bit 0: code 1, bit 1: code 2) give up at once."""
+        flups_debug_wait_limit(self._s, mask)
 
     def check(self) -> int:
         """Device-side status since the last check (0, or the code of a bounded wait that gave up)."""

@@ -72,3 +72,37 @@ def gaussian_potential(r, sigma):
     nz = r > 0
     out[nz] = -erf(r[nz] / (math.sqrt(2.0) * sigma)) / (4.0 * math.pi * r[nz])
     return out
+
+
+def vortex_tube(N, nz, R, L=1.0):
+    """The paper's Biot-Savart validation (Section "Application: the Biot-Savart solver"): a compact
+    vortex tube along z centred at (L/2, L/2), radius R, node-centred N + 1 points in x and y and
+    nz + 1 in z.  Returns (f, u): f = (0, 0, -w(r)) with w(r) = (1/2 pi)(2/R^2)(1/E2(1))
+    exp(-1/(1 - (r/R)^2)) inside R (the field handed to the solver, lap(u) = curl f) and the
+    analytical velocity u = (-sin(theta) u_t, cos(theta) u_t, 0) with
+    u_t(r) = (1/(2 pi r)) [1 - (1 - (r/R)^2) E2(1/(1 - (r/R)^2)) / E2(1)] inside R, 1/(2 pi r) outside.
+    Arrays are [c, z, y, x]."""
+    from scipy.special import expn
+    x = np.arange(N + 1) * (L / N) - 0.5 * L
+    X, Y = np.meshgrid(x, x, indexing="xy")        # [y, x]
+    r = np.sqrt(X * X + Y * Y)
+    q = (r / R) ** 2
+    inside = q < 1.0
+    e21 = expn(2, 1.0)
+    w = np.zeros_like(r)
+    w[inside] = (1.0 / (2 * math.pi)) * (2.0 / (R * R)) / e21 * np.exp(-1.0 / (1.0 - q[inside]))
+    ut = np.zeros_like(r)
+    rr = np.where(r > 0, r, 1.0)
+    ut_out = 1.0 / (2 * math.pi * rr)
+    s = np.where(inside, 1.0 - q, 1.0)
+    ut_in = ut_out * (1.0 - s * expn(2, 1.0 / s) / e21)
+    ut = np.where(inside, ut_in, ut_out)
+    ut = np.where(r > 0, ut, 0.0)
+    ux = -Y / rr * ut
+    uy = X / rr * ut
+    f = np.zeros((3, nz + 1, N + 1, N + 1))
+    f[2] = -w[None, :, :]
+    u = np.zeros_like(f)
+    u[0] = ux[None]
+    u[1] = uy[None]
+    return f, u

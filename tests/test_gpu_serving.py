@@ -47,6 +47,53 @@ def test_results_alone_equal_results_in_the_mix():
         assert np.abs(got - ref).max() <= tol * max(np.abs(ref).max(), 1e-300), r.rid
 
 
+def _oracle(req):
+    """The FP64 oracle's result for a served request: oracle.solve, or oracle.biot_savart with the
+    per-component face conditions the server applies (serve.vector_bc)."""
+    import oracle
+    f = W.request_rhs(req)
+    h = tuple(1.0 / v for v in req.n)
+    kernel = "hej2" if req.kernel == F.HEJ2 else "spectral"
+    if req.op == F.BIOT_SAVART:
+        return oracle.biot_savart(f, serve.vector_bc(req.bc), h, center=oracle.CELL, kernel=kernel)
+    return oracle.solve(f, oracle.Problem(bc=req.bc, h=h, center=oracle.CELL, kernel=kernel))
+
+
+def _extra_requests(rid0):
+    """32^3 and 64^3 requests with unbounded, semi-unbounded and symmetric faces, both precisions,
+    Poisson and Biot-Savart, arriving in the same stream."""
+    E, O, P, U = F.EVEN, F.ODD, F.PER, F.UNB
+    specs = [
+        ((32, 32, 32), ((U, U), (E, O), (P, P)), 0, F.F64),
+        ((64, 64, 64), ((O, U), (U, E), (U, U)), 0, F.F32),
+        ((64, 64, 64), ((E, E), (O, O), (U, U)), 0, F.F64),
+        ((32, 32, 32), ((U, U), (U, U), (E, U)), 1, F.F64),
+        ((64, 64, 64), ((U, U), (U, U), (O, E)), 1, F.F32),
+        ((32, 32, 32), ((P, P), (P, P), (O, O)), 1, F.F64),
+    ]
+    out = []
+    for i, (n, bc, op, prec) in enumerate(specs):
+        kernel = F.HEJ2 if any(F.UNB in b for b in bc) else F.SPECTRAL
+        out.append(W.Request(rid=rid0 + i, arrival_s=0.0, n=n, bc=bc, op=op, prec=prec, kernel=kernel))
+    return out
+
+
+def test_served_results_match_the_oracle():
+    """Every result of a mixed stream (sizes 16-64, random face conditions, Biot-Savart vortex rings,
+    FP32 and FP64, solved concurrently in slots) against the FP64 oracle, element by element:
+    rel. L-inf <= 1e-12 (FP64) or 1e-5 (FP32) of the whole field's max."""
+    reqs = _small_stream() + _extra_requests(1000)
+    out = serve.run_stream(reqs, 512 << 20, nstreams=4, closed_loop=True, keep={r.rid for r in reqs})
+    assert out["completed"] == len(reqs) and out["errors"] == 0
+    assert any(r.op == F.BIOT_SAVART for r in reqs) and any(r.prec == F.F32 for r in reqs)
+    for r in reqs:
+        ref = _oracle(r)
+        got = out["outputs"][r.rid].numpy().astype(np.float64).reshape(ref.shape)
+        tol = 1e-12 if r.prec == F.F64 else 1e-5
+        err = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+        assert err <= tol, (r.rid, r.n, r.bc, r.op, r.prec, err)
+
+
 def _need(req):
     """Device bytes of one plan plus one slot for this request (host-only query)."""
     r = serve.c_request(req)
