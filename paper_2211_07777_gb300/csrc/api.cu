@@ -351,7 +351,7 @@ void fill_geom(Launch& L, const DirPlan& dp, int axis, const int* din, const int
   p.axis = axis;
   p.npen = axis == 0 ? din[1] * din[2] : din[0];
   int W, nthr;
-  int wct = share == 1 ? ct_tile_width(dp.P, prec) : 0;  // the curl pass keeps the runtime engine
+  int wct = share == 1 ? ct_tile_width(dp.P, prec, axis, L.kind) : 0;  // the curl pass keeps the runtime engine
   const int other = axis == 0 ? 1 : (axis == 1 ? din[2] : din[1]);
   auto ctas = [&](int w) { return (long long)((p.npen + (packed ? 2 * w : w) - 1) / (packed ? 2 * w : w)) * other * ncomp; };
   if (wct && ctas(wct) < 2 * 152) wct = 0;  // small grid: narrower runtime tiles, more CTAs
@@ -398,7 +398,7 @@ void fill_geom(Launch& L, const DirPlan& dp, int axis, const int* din, const int
     // column kernels: 128-byte alignment of the tile and a 128-byte block for their mbarriers;
     // EPT elements per thread and stage
     L.smem += 256;
-    p.ept = ct_col_ept(dp.P, prec);
+    p.ept = ct_col_ept(dp.P, prec, L.kind);
     L.nthr = dp.P * W / p.ept;
   }
 }
@@ -1168,7 +1168,7 @@ static int solve_impl(flups_solver s, void* phi, const void* rhs, void* ws, void
     status = (int*)((char*)ws + s->ws_need - kStatusBlock);
     CK(cudaMemsetAsync(status, 0, sizeof(int), st));
   }
-  for (Launch& L : s->passes) {
+  auto launch_one = [&](const Launch& L) -> int {
     Launch Lw = L;
     PassParams& p = Lw.p;
     p.errflag = status;
@@ -1178,9 +1178,14 @@ static int solve_impl(flups_solver s, void* phi, const void* rhs, void* ws, void
     if (L.user_in) p.in = rhs;
     if (L.user_out) p.out = phi;
     if (ws && L.in_buf) encode_input_map(Lw, prec);  // the caller's workspace: maps of its addresses
-    cudaError_t e = L.kind >= K_CURL_REAL ? launch_curl(L.kind, prec, p, L.grid, L.nthr, L.smem, st)
-                                          : launch_pass(L.kind, prec, p, L.grid, L.nthr, L.smem, st);
+    cudaError_t e = L.kind >= K_CURL_REAL ? launch_curl(L.kind, prec, p, Lw.grid, L.nthr, L.smem, st)
+                                          : launch_pass(L.kind, prec, p, Lw.grid, L.nthr, L.smem, st);
     if (e) return cuda_fail(e, "pass launch");
+    return FLUPS_OK;
+  };
+  for (const Launch& L : s->passes) {
+    const int rc = launch_one(L);
+    if (rc) return rc;
   }
   return FLUPS_OK;
 }

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "dfloat.cuh"
 
 namespace flups {
@@ -400,13 +402,22 @@ __host__ __device__ constexpr int ct_radix(int rem) {
   return rem == 32 ? 8 : (rem >= 16 ? 16 : rem);
 }
 
+// Shared-memory layout of the compile-time engine's tile: element (row i, lane l) of W lanes, rows
+// padded to W + 1 elements so that the transposing row-mode accesses (32 consecutive rows of one
+// lane) hit distinct banks.  (An XOR swizzle of the 4-lane FP32 tiles removes the stages' bank
+// conflicts -- 3.8 wavefronts per access to the minimum 2 -- but its index arithmetic made the
+// integer pipe the bottleneck of the x passes: forward 0.643 -> 0.713 ms at 512^3; not used.)
+template <typename T, int W> struct CtTile {
+  __host__ __device__ static constexpr int at(int i, int l) { return i * (W + 1) + l; }
+};
+
 // ZIN: the stage's inputs with r >= R/2 are zero (first stage of a transform
 // whose second half is zero padding); ZOUT: its outputs with r >= R/2 are not
 // needed (last stage of a transform truncated to its first half).  Both are
 // compile-time, so the loads, stores and dead butterfly arithmetic vanish.
 template <typename T, int P, int W, int NT, int R, int Ns, bool INV, bool ZIN = false, bool ZOUT = false>
 __device__ __forceinline__ void ct_stage(cpx<T>* S, const cpx<T>* __restrict__ tw, int tid) {
-  constexpr int LS = W + 1;
+  using TL = CtTile<T, W>;
   constexpr int nbf = P / R;
   constexpr int NB = (nbf * W) / NT;
   static_assert((nbf * W) % NT == 0, "tile and block do not match");
@@ -417,7 +428,7 @@ __device__ __forceinline__ void ct_stage(cpx<T>* S, const cpx<T>* __restrict__ t
     const int idx = tid + b * NT;
     const int lane = idx % W, j = idx / W, k = j % Ns;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[b][r] = (ZIN && r >= R / 2) ? mk<T>((T)0, (T)0) : S[(j + r * nbf) * LS + lane];
+    for (int r = 0; r < R; ++r) v[b][r] = (ZIN && r >= R / 2) ? mk<T>((T)0, (T)0) : S[TL::at(j + r * nbf, lane)];
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
@@ -434,7 +445,7 @@ __device__ __forceinline__ void ct_stage(cpx<T>* S, const cpx<T>* __restrict__ t
     const int lane = idx % W, j = idx / W, k = j % Ns;
     const int base = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < (ZOUT ? R / 2 : R); ++r) S[(base + r * Ns) * LS + lane] = v[b][r];
+    for (int r = 0; r < (ZOUT ? R / 2 : R); ++r) S[TL::at(base + r * Ns, lane)] = v[b][r];
   }
   __syncthreads();
 }
@@ -494,7 +505,7 @@ __host__ __device__ constexpr int ct_ns_rev_e(int P, int s, int ept) {
   return ns;
 }
 
-// In-place transform of the tile in S (lane stride W + 1); ends with a barrier.
+// In-place transform of the tile in S (layout CtTile<T, W>); ends with a barrier.
 template <typename T, int P, int W, bool INV, bool ZIN = false, bool ZOUT = false>
 __device__ __forceinline__ void fft_tile_ct(cpx<T>* S, const cpx<T>* __restrict__ tw, int tid) {
   ct_stages<T, P, W, P * W / 16, 1, INV, ZIN, ZOUT>(S, tw, tid);

@@ -20,6 +20,13 @@ template <> __device__ __forceinline__ void st_real<dfloat>(dfloat* a, long long
   else reinterpret_cast<float2*>(a)[off] = make_float2(v.hi, v.lo);
 }
 
+// Index of element (row i, lane l) of a tile: the compile-time engine's layout (WC > 0) or rows of
+// LS elements (runtime engine).
+template <typename T, int WC> __device__ __forceinline__ int tix(int i, int l, int LS) {
+  if constexpr (WC > 0) return CtTile<T, WC>::at(i, l);
+  else return i * LS + l;
+}
+
 // Transform type of component `comp` (4 bits per component).
 __device__ __forceinline__ int comp_type(const PassParams& p, int comp) { return (p.ctypes >> (4 * comp)) & 15; }
 
@@ -112,14 +119,14 @@ __device__ __forceinline__ int primary_pos(int t, int center, int N, int i) {
 // ---------------------------------------------------------------------------
 // Shared helpers.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int WC = 0>
 __device__ __forceinline__ void zero_fill(cpx<T>* S, int LS, int W, int lo, int hi, int tid, int nthr) {
   // W is a power of two
   const int tot = (hi - lo) * W;
   for (int idx = tid; idx < tot; idx += nthr) {
     const int lane = idx & (W - 1);
     const int j = lo + idx / W;
-    S[j * LS + lane] = mk<T>((T)0, (T)0);
+    S[tix<T, WC>(j, lane, LS)] = mk<T>((T)0, (T)0);
   }
 }
 
@@ -133,7 +140,7 @@ __device__ __forceinline__ void load_real_ext(const PassParams& p, int type, con
   const bool rev = is_reversed(type);
   int lo[3], hi[3];
   const int nz = skip_zero ? 0 : zero_ranges(t, p.center, N, lo, hi);
-  for (int r = 0; r < nz; ++r) zero_fill<T>(S, LS, W, lo[r], hi[r], tid, nthr);
+  for (int r = 0; r < nz; ++r) zero_fill<T, WC>(S, LS, W, lo[r], hi[r], tid, nthr);
   T* Sr = reinterpret_cast<T*>(S);
   const int W2 = 2 * W;
   const bool rowmode = p.axis == 0;
@@ -170,7 +177,7 @@ __device__ __forceinline__ void load_real_ext(const PassParams& p, int type, con
         int pos[4], sg[4];
         const int n = images(t, p.center, N, dix, pos, sg);
         for (int k = 0; k < n; ++k)
-          S[pos[k] * LS + ll[u]] = sg[k] > 0 ? mk<T>(va[u], vb[u]) : mk<T>(-va[u], -vb[u]);
+          S[tix<T, WC>(pos[k], ll[u], LS)] = sg[k] > 0 ? mk<T>(va[u], vb[u]) : mk<T>(-va[u], -vb[u]);
       }
     }
     return;
@@ -203,7 +210,7 @@ __device__ __forceinline__ void load_real_ext(const PassParams& p, int type, con
       int pos[4], sg[4];
       const int n = images(t, p.center, N, dix, pos, sg);
       const int lane = cc[u] >> 1, part = cc[u] & 1;
-      for (int k = 0; k < n; ++k) Sr[2 * (pos[k] * LS + lane) + part] = sg[k] > 0 ? v[u] : -v[u];
+      for (int k = 0; k < n; ++k) Sr[2 * tix<T, WC>(pos[k], lane, LS) + part] = sg[k] > 0 ? v[u] : -v[u];
     }
   }
 }
@@ -231,7 +238,7 @@ __device__ __forceinline__ void store_real_data(const PassParams& p, int type, T
       const int ii = rev ? nd - 1 - i : i;
       const int pos = primary_pos(t, p.center, N, ii);
       cpx<T> z = mk<T>((T)0, (T)0);
-      if (pos >= 0) z = S[pos * LS + lane];
+      if (pos >= 0) z = S[tix<T, WC>(pos, lane, LS)];
       const long long off = (long long)qa * p.ao.ls + (long long)i * p.ao.js;
       st_real<T>(out, off, z.x, p.out_f64);
       if (qa + 1 < p.npen) st_real<T>(out, off + p.ao.ls, z.y, p.out_f64);
@@ -249,7 +256,7 @@ __device__ __forceinline__ void store_real_data(const PassParams& p, int type, T
     const int pos = primary_pos(t, p.center, N, ii);
     T v = (T)0;
     if (pos >= 0) {
-      const cpx<T> z = S[pos * LS + (c >> 1)];
+      const cpx<T> z = S[tix<T, WC>(pos, c >> 1, LS)];
       v = (c & 1) ? z.y : z.x;
     }
     st_real<T>(out, (long long)q * p.ao.ls + (long long)i * p.ao.js, v, p.out_f64);
@@ -268,7 +275,7 @@ template <typename T, int WC = 0>
 __device__ __forceinline__ void load_cplx(const PassParams& p, const cpx<T>* __restrict__ in, cpx<T>* S, int q0,
                                           int tid, int nthr, bool skip_zero = false) {
   const int W = WC ? WC : p.W, LS = WC ? WC + 1 : p.LS, nu = p.n_use;
-  if (nu < p.P && !skip_zero) zero_fill<T>(S, LS, W, nu, p.P, tid, nthr);
+  if (nu < p.P && !skip_zero) zero_fill<T, WC>(S, LS, W, nu, p.P, tid, nthr);
   const bool rowmode = p.axis == 0;
   const int tot = rowmode ? (W << p.ndlog) : nu * W;
   constexpr int LOADB = 8;
@@ -290,7 +297,7 @@ __device__ __forceinline__ void load_cplx(const PassParams& p, const cpx<T>* __r
     }
 #pragma unroll
     for (int u = 0; u < LOADB; ++u)
-      if (ii[u] >= 0) S[ii[u] * LS + ll[u]] = v[u];
+      if (ii[u] >= 0) S[tix<T, WC>(ii[u], ll[u], LS)] = v[u];
   }
 }
 
@@ -307,7 +314,7 @@ __device__ __forceinline__ void store_cplx_data(const PassParams& p, cpx<T>* __r
     const int q = q0 + lane;
     if (q >= p.npen) continue;
     const int pos = (p.type == T_PER && p.center == C_NODE && i == p.N) ? 0 : i;
-    out[(long long)q * p.ao.ls + (long long)i * p.ao.js] = S[pos * LS + lane];
+    out[(long long)q * p.ao.ls + (long long)i * p.ao.js] = S[tix<T, WC>(pos, lane, LS)];
   }
 }
 

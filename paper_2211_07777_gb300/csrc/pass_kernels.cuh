@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
       if (qa >= p.npen) continue;
       const int kk = quarter ? 2 * k + 1 : k;
       const int km = kk == 0 ? 0 : P - kk;
-      const cpx<T> zk = S[kk * LS + lane], zm = S[km * LS + lane];
+      const cpx<T> zk = S[tix<T, WC>(kk, lane, LS)], zm = S[tix<T, WC>(km, lane, LS)];
       store_mode(qa, k, kk, split<T>(zk, zm, 0));
       if (qa + 1 < p.npen) store_mode(qa + 1, k, kk, split<T>(zk, zm, 1));
     }
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     const int lane = c >> 1, part = c & 1;
     const int kk = quarter ? 2 * k + 1 : k;
     const int km = kk == 0 ? 0 : P - kk;
-    store_mode(q, k, kk, split<T>(S[kk * LS + lane], S[km * LS + lane], part));
+    store_mode(q, k, kk, split<T>(S[tix<T, WC>(kk, lane, LS)], S[tix<T, WC>(km, lane, LS)], part));
   }
 }
 
@@ -208,8 +208,8 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
         if (nyq && !(last && tid < W)) continue;
         const int idx = tid + u * nthr;
         const int lane = nyq ? tid : idx / HP, k = nyq ? HP : idx % HP;
-        S[k * LS + lane] = mk<T>(Xa[e].x - Xb[e].y, Xa[e].y + Xb[e].x);
-        if (k != 0 && 2 * k != P) S[(P - k) * LS + lane] = mk<T>(Xa[e].x + Xb[e].y, Xb[e].x - Xa[e].y);
+        S[tix<T, WC>(k, lane, LS)] = mk<T>(Xa[e].x - Xb[e].y, Xa[e].y + Xb[e].x);
+        if (k != 0 && 2 * k != P) S[tix<T, WC>(P - k, lane, LS)] = mk<T>(Xa[e].x + Xb[e].y, Xb[e].x - Xa[e].y);
       }
     }
   }
@@ -240,8 +240,8 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
       const int k = kk[u];
       if (k < 0) continue;
       const int lane = ll[u];
-      S[k * LS + lane] = mk<T>(Xa[u].x - Xb[u].y, Xa[u].y + Xb[u].x);
-      if (k != 0 && 2 * k != P) S[(P - k) * LS + lane] = mk<T>(Xa[u].x + Xb[u].y, Xb[u].x - Xa[u].y);
+      S[tix<T, WC>(k, lane, LS)] = mk<T>(Xa[u].x - Xb[u].y, Xa[u].y + Xb[u].x);
+      if (k != 0 && 2 * k != P) S[tix<T, WC>(P - k, lane, LS)] = mk<T>(Xa[u].x + Xb[u].y, Xb[u].x - Xa[u].y);
     }
   }
   __syncthreads();
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     if (rowmode) { k = idx % P; lane = idx / P; } else { lane = idx & (W - 1); k = idx / W; }
     const int q = q0 + lane;
     if (q >= p.npen) continue;
-    out[(long long)q * p.ao.ls + (long long)k * p.ao.js] = S[k * LS + lane];
+    out[(long long)q * p.ao.ls + (long long)k * p.ao.js] = S[tix<T, WC>(k, lane, LS)];
   }
 }
 
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     const int q = q0 + lane;
     cpx<T> v = mk<T>((T)0, (T)0);
     if (q < p.npen) v = in[(long long)q * p.ai.ls + (long long)k * p.ai.js];
-    S[k * LS + lane] = v;
+    S[tix<T, WC>(k, lane, LS)] = v;
   }
   __syncthreads();
   S = run_fft<T, PC, WC, true, false, HZ>(p, S, second_buffer<T, PC>(p, S), (const cpx<T>*)p.tw, tid, nthr);
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     const int lane = idx & (W - 1), k = idx / W;
     const int g3 = min(k, P - k);
     const T G = green_at<T>(p, goff[lane], k2p[lane], g3);
-    X[k * LS + lane] = cscale<T>(X[k * LS + lane], G);
+    X[tix<T, WC>(k, lane, LS)] = cscale<T>(X[tix<T, WC>(k, lane, LS)], G);
   }
   __syncthreads();
   X = run_fft<T, PC, WC, true, false, HZ>(p, X, X == S ? S2 : S, tw, tid, nthr);
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   for (int idx = tid; idx < tot; idx += nthr) {
     const int lane = idx & (W - 1), k = idx / W;
     const int km = k == 0 ? 0 : P - k;
-    const cpx<T> zk = X[k * LS + lane], zm = X[km * LS + lane];
+    const cpx<T> zk = X[tix<T, WC>(k, lane, LS)], zm = X[tix<T, WC>(km, lane, LS)];
     cpx<T> A = split<T>(zk, zm, 0), B = split<T>(zk, zm, 1);
     if (quarter && (k & 1) == 0) {
       A = mk<T>((T)0, (T)0);
@@ -433,8 +433,8 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
       A = cscale<T>(A, Ga);
       B = cscale<T>(B, Gb);
     }
-    X[k * LS + lane] = mk<T>(A.x - B.y, A.y + B.x);
-    if (k != 0 && 2 * k != P) X[km * LS + lane] = mk<T>(A.x + B.y, B.x - A.y);
+    X[tix<T, WC>(k, lane, LS)] = mk<T>(A.x - B.y, A.y + B.x);
+    if (k != 0 && 2 * k != P) X[tix<T, WC>(km, lane, LS)] = mk<T>(A.x + B.y, B.x - A.y);
   }
   __syncthreads();
   X = run_fft<T, PC, WC, true, false, HZ>(p, X, X == S ? S2 : S, tw, tid, nthr);
@@ -539,7 +539,10 @@ __device__ __forceinline__ void xstage(cpx<T>* S, cpx<T>* v, const cpx<T>* __res
         }
       }
     }
-    if constexpr (SRC == XS_SMEM || SRC == XS_NAT) __syncthreads();
+    // every thread has read its inputs before any thread overwrites them: needed when this stage
+    // (or, from registers, the next one) writes shared memory; a last stage that stores to global
+    // memory writes none
+    if constexpr ((SRC == XS_SMEM || SRC == XS_NAT) && DST != XS_GLOBAL) __syncthreads();
   }
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
@@ -812,7 +815,8 @@ __global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<
 // ---------------------------------------------------------------------------
 // Instantiation helpers: one launcher and one smem-limit setter per <T, PC, WC>.
 // ---------------------------------------------------------------------------
-// Column kernels with radix-32 stages (32 elements per thread) are compiled for FP32 at P = 1024.
+// Column kernels with radix-32 stages (32 elements per thread) are compiled for FP32 at P = 1024
+// (the planner uses them for the fused pass).
 template <typename T, int PC> constexpr bool has_ept32() { return std::is_same<T, float>::value && PC == 1024; }
 
 template <typename T, int PC, int WC, bool HZ>

@@ -5,7 +5,11 @@
 
 namespace flups {
 
-int ct_tile_width(int P, int prec) {
+int ct_tile_width(int P, int prec, int axis, int kind) {
+  // FP32 at P = 1024 (measured at 512^3): 4 lanes for the x passes (row mode) and for the
+  // single-transform column passes (radix-32, 128 threads: more CTAs per SM to overlap their
+  // memory phases); 8 lanes for the fused column pass and the other passes
+  if (prec == 0 && P == 1024 && (axis == 0 || kind == K_FWD_C2C || kind == K_INV_C2C)) return 4;
   // lanes per tile: ~32-96 KB of shared memory, 16 elements per thread
   switch (P) {
     case 32: return prec == 0 ? 64 : 32;
@@ -19,7 +23,11 @@ int ct_tile_width(int P, int prec) {
   return 0;
 }
 
-int ct_col_ept(int P, int prec) { return (prec == 0 && P == 1024) ? 32 : 16; }
+int ct_col_ept(int P, int prec, int kind) {
+  // radix-32 stages (1024 = 32 x 32) for every FP32 column pass at P = 1024: the fused pass with
+  // 8-lane tiles (256 threads), the single-transform passes with 4-lane tiles (128 threads)
+  return (prec == 0 && P == 1024) ? 32 : 16;
+}
 
 cudaError_t set_pass_smem_limits() {
   cudaError_t e = set_limits_kind<float, 0, 0>();

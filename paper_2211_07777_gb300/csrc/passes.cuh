@@ -91,10 +91,13 @@ cudaError_t launch_curl(int kind, int prec, const PassParams& p, dim3 grid, int 
 cudaError_t set_curl_smem_limits();
 cudaError_t launch_pass(int kind, int prec, const PassParams& p, dim3 grid, int nthreads, size_t smem, cudaStream_t st);
 cudaError_t set_pass_smem_limits();
-// compile-time tile engine: lanes per tile for P = 2^a (32 <= P <= 2048), 0 when not compiled
-int ct_tile_width(int P, int prec);
-// compile-time column passes: elements per thread and stage (32: radix-32 stages), 16 otherwise
-int ct_col_ept(int P, int prec);
+
+// compile-time tile engine: lanes per tile for P = 2^a (32 <= P <= 2048) of a pass along `axis`
+// of kind `kind`, 0 when not compiled
+int ct_tile_width(int P, int prec, int axis, int kind);
+// compile-time column passes of kind `kind`: elements per thread and stage (32: radix-32 stages),
+// 16 otherwise
+int ct_col_ept(int P, int prec, int kind);
 cudaError_t launch_ct_f32(int P, int kind, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st);
 cudaError_t launch_ct_f64(int P, int kind, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st);
 cudaError_t set_limits_ct_f32();
