@@ -803,6 +803,31 @@ void encode_input_map(Launch& L, int prec) {
   p.tin_box = box;
 }
 
+// Inverse row pass (x) of complex modes: its CTA's 2W input rows, contiguous in memory, arrive in
+// shared memory by one bulk copy instead of per-thread loads whose latency the pass could not hide
+// (unbounded 512^3 FP32: long-scoreboard stalls were its largest).  Used where the rows are 16-byte
+// aligned and the extra shared memory still leaves two CTAs per SM.
+void set_rows_bulk(Launch& L, int prec) {
+  PassParams& p = L.p;
+  if (p.rows_bulk) {
+    L.smem = p.rows_off - 128;  // back to the size without the staged rows
+    p.rows_bulk = 0;
+  }
+  if (L.kind != K_INV_REAL || !p.ct || p.axis != 0 || prec != FLUPS_F32 || !p.in) return;
+  for (int c = 0; c < 3; ++c) {
+    const int t = (p.ctypes >> (4 * c)) & 15;
+    if (t != T_PER && t != T_UNB) return;
+  }
+  const size_t cb = 2 * esize(prec);
+  if (((uintptr_t)p.in % 16) != 0 || (p.ai.ls * cb) % 16 != 0 || (p.ai.cs * cb) % 16 != 0) return;
+  const size_t off = ((L.smem + 15) & ~(size_t)15) + 128;  // 128 bytes for the mbarrier
+  const size_t total = off + (size_t)2 * p.W * p.ai.ls * cb;
+  if (2 * total > 227 * 1024) return;
+  p.rows_off = (int)off;
+  p.rows_bulk = 1;
+  L.smem = total;
+}
+
 int build_passes(flups_solver_s* s, cudaStream_t st) {
   const int prec = s->topo.prec, center = s->topo.center, nc = s->topo.ncomp;
   const int* o = s->order;
@@ -1147,6 +1172,7 @@ int flups_setup(flups_solver s, void* stream, size_t* workspace_bytes) {
   for (Launch& L : s->passes) {
     L.p.errflag = s->errflag;
     encode_input_map(L, prec);
+    set_rows_bulk(L, prec);
   }
   CK(cudaStreamSynchronize(st));
   s->user_bytes = (size_t)s->topo.n[0] * s->topo.n[1] * s->topo.n[2] * nc * es;
@@ -1177,9 +1203,12 @@ static int solve_impl(flups_solver s, void* phi, const void* rhs, void* ws, void
     if (L.out_buf) p.out = W[L.out_buf];
     if (L.user_in) p.in = rhs;
     if (L.user_out) p.out = phi;
-    if (ws && L.in_buf) encode_input_map(Lw, prec);  // the caller's workspace: maps of its addresses
-    cudaError_t e = L.kind >= K_CURL_REAL ? launch_curl(L.kind, prec, p, Lw.grid, L.nthr, L.smem, st)
-                                          : launch_pass(L.kind, prec, p, Lw.grid, L.nthr, L.smem, st);
+    if (ws && L.in_buf) {  // the caller's workspace: maps and alignment of its addresses
+      encode_input_map(Lw, prec);
+      set_rows_bulk(Lw, prec);
+    }
+    cudaError_t e = L.kind >= K_CURL_REAL ? launch_curl(L.kind, prec, p, Lw.grid, Lw.nthr, Lw.smem, st)
+                                          : launch_pass(L.kind, prec, p, Lw.grid, Lw.nthr, Lw.smem, st);
     if (e) return cuda_fail(e, "pass launch");
     return FLUPS_OK;
   };

@@ -110,6 +110,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, int* 
   while (!done && global_ns() - t1 < kDrainLimitNs) done = mbar_try_wait(bar, 0);
   return false;
 }
+// 1D bulk copy of `bytes` contiguous bytes from global to shared memory, completed on an mbarrier
+// (both addresses 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
 // 3D tile load of the box at coordinates (c0, c1, c2) of the tensor map into shared memory
 __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int c0, int c1, int c2,
                                             unsigned long long* bar) {

@@ -183,6 +183,30 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     // lane = idx / (P/2) keeps k fastest (coalesced); the Nyquist modes k = P/2 go to threads
     // tid < W with the last batch
     constexpr int HP = PC / 2, NB8 = 8, IB = 4;
+    // with p.rows_bulk the CTA's rows q0 .. q0 + 2W - 1 (complex modes, rows p.ai.ls apart) are first
+    // copied into shared memory by one bulk copy, and the modes are read from there
+    const cpx<T>* rows = nullptr;
+    if (p.rows_bulk) {
+      unsigned char* sb = smraw + p.rows_off;
+      unsigned long long* bar = reinterpret_cast<unsigned long long*>(sb) - 16;
+      const int nrows = min(2 * W, p.npen - q0);
+      if (tid == 0) mbar_init(bar, 1);
+      __syncthreads();
+      if (tid == 0) {
+        const unsigned bytes = (unsigned)((size_t)nrows * p.ai.ls * sizeof(cpx<T>));
+        mbar_expect_tx(bar, bytes);
+        bulk_load(sb, (const cpx<T>*)p.in + obase_i + (long long)q0 * p.ai.ls, bytes, bar);
+      }
+      const bool ok = mbar_wait_bounded(bar, p.errflag, 2, p.dbg_wait & 2);
+      if (__syncthreads_or(!ok)) return;  // the tile's input did not arrive in time: no stores
+      rows = reinterpret_cast<const cpx<T>*>(sb);
+    }
+    auto mode = [&](int q, int k) -> cpx<T> {
+      if (!rows) return stored_mode<T>(p, ctype, p.in, obase_i + (long long)q * p.ai.ls, k, P, tw);
+      cpx<T> X = rows[(long long)(q - q0) * p.ai.ls + k];
+      if (k == 0 || 2 * k == P) X.y = (T)0;  // DC and Nyquist of a real signal are real
+      return X;
+    };
 #pragma unroll
     for (int u0 = 0; u0 < NB8; u0 += IB) {
       constexpr int NI = IB + 1;
@@ -198,8 +222,8 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
         Xa[e] = mk<T>((T)0, (T)0);
         Xb[e] = Xa[e];
         if (nyq && !(last && tid < W)) continue;
-        if (qa < p.npen) Xa[e] = stored_mode<T>(p, ctype, p.in, obase_i + (long long)qa * p.ai.ls, k, P, tw);
-        if (qb < p.npen) Xb[e] = stored_mode<T>(p, ctype, p.in, obase_i + (long long)qb * p.ai.ls, k, P, tw);
+        if (qa < p.npen) Xa[e] = mode(qa, k);
+        if (qb < p.npen) Xb[e] = mode(qb, k);
       }
 #pragma unroll
       for (int e = 0; e < NI; ++e) {

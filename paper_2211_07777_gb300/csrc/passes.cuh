@@ -73,6 +73,10 @@ struct PassParams {
   int gbox;               // rows per box of the first tensor map
   int* errflag;           // device word: set to a nonzero code when a bounded wait gives up
   int dbg_wait;           // test hook: bit (code - 1) set makes the bounded wait of that code give up at once
+  int rows_bulk;          // inverse row pass of complex modes: the CTA's 2W input rows arrive by one bulk
+                          // copy into shared memory at byte offset rows_off (after the tile) instead of
+                          // per-thread loads
+  int rows_off;
   // column passes of the compile-time engine: the input tile by TMA (0 rows: loads from registers)
   int tin_rows;           // rows along the axis copied into the tile (P/2 when pruned, else P)
   int tin_box;            // rows per TMA box
