@@ -161,7 +161,8 @@ int flups_solve_events(flups_solver s, void* phi, const void* rhs, void* stream,
 int flups_pass_info(flups_solver s, int i, int* kind, int* axis, int* fft_len, double* bytes, double* flops);
 /* How pass i runs (bit flags): 1 compile-time tile engine, 2 Green slice staged in shared memory
  * ahead of the multiply, 4 that slice copied by TMA (tensor map + mbarrier), 8 doubled transform
- * pruned to its nonzero half, 16 input tile copied by TMA (tensor map + mbarrier).  Introspection
+ * pruned to its nonzero half, 16 input tile copied by TMA (tensor map + mbarrier), 32 x pass on the
+ * column kernels' register-chained stages, 64 input rows staged by one bulk copy.  Introspection
  * only; no counterpart in the paper. */
 int flups_pass_features(flups_solver s, int i, int* flags);
 

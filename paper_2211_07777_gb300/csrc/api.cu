@@ -803,6 +803,28 @@ void encode_input_map(Launch& L, int prec) {
   p.tin_box = box;
 }
 
+// x passes of periodic or doubled unbounded cell-centred real data in 4-lane FP32 tiles run on the
+// column kernels' register-chained stages (k_fwd_rowx, k_inv_rowx): the generic row kernels spent
+// about 100-120 instructions per element on one transform and half their shared-memory
+// wavefronts on bank conflicts (unbounded 512x256x256 FP32 under ncu).
+void set_rowx(Launch& L, int prec) {
+  PassParams& p = L.p;
+  p.rowx = 0;
+  if (!p.ct || p.axis != 0 || prec != FLUPS_F32 || p.W != 4 || p.center != C_CELL) return;
+  if (L.kind != K_FWD_REAL && L.kind != K_INV_REAL) return;
+  for (int c = 0; c < (int)L.grid.z; ++c) {
+    const int t = (p.ctypes >> (4 * c)) & 15;
+    if (!((t == T_UNB && 2 * p.n_data == p.P) || (t == T_PER && p.n_data == p.P))) return;
+  }
+  p.rowx = 1;
+  // measured at 512^3 (P = 1024): the forward pass runs best with 16 elements per thread (256
+  // threads; 0.488 vs 0.516 ms with radix-32 stages), the inverse with radix-32 stages and its
+  // rows staged by a bulk copy (0.453 ms; 0.492 with 16 elements per thread)
+  p.ept = L.kind == K_FWD_REAL ? 16 : ct_col_ept(p.P, prec, K_FWD_C2C);
+  L.nthr = p.P * p.W / p.ept;
+  L.smem = (size_t)p.P * (p.W + 1) * 2 * esize(prec) + 256;
+}
+
 // Inverse row pass (x) of complex modes: its CTA's 2W input rows, contiguous in memory, arrive in
 // shared memory by one bulk copy instead of per-thread loads whose latency the pass could not hide
 // (unbounded 512^3 FP32: long-scoreboard stalls were its largest).  Used where the rows are 16-byte
@@ -967,6 +989,7 @@ int build_passes(flups_solver_s* s, cudaStream_t st) {
     bytes += L.bytes;
   }
   s->model_bytes = bytes;
+  for (Launch& L : s->passes) set_rowx(L, prec);  // before set_rows_bulk (flups_setup): the staged rows follow the tile
   for (const Launch& L : s->passes)
     if (L.smem > 227 * 1024 || L.nthr > 1024) return FLUPS_ESIZE;
   return FLUPS_OK;
@@ -1368,7 +1391,8 @@ int flups_pass_features(flups_solver s, int i, int* flags) {
   if (!s->ready) return FLUPS_ESTATE;
   if (i < 0 || i >= (int)s->passes.size()) return FLUPS_EINVAL;
   const PassParams& p = s->passes[i].p;
-  *flags = (p.ct ? 1 : 0) | (p.gpre ? 2 : 0) | (p.gmap ? 4 : 0) | (p.hz ? 8 : 0) | (p.tin_rows ? 16 : 0);
+  *flags = (p.ct ? 1 : 0) | (p.gpre ? 2 : 0) | (p.gmap ? 4 : 0) | (p.hz ? 8 : 0) | (p.tin_rows ? 16 : 0) |
+           (p.rowx ? 32 : 0) | (p.rows_bulk ? 64 : 0);
   return FLUPS_OK;
 }
 

@@ -509,6 +509,11 @@ struct ColRows {
       for (; x > 0; x >>= LG) f ^= x & (G - 1);
     return f;
   }
+  // shared-memory element of natural row o, lane l, after a stage that stored to shared memory
+  __device__ __forceinline__ static int at(int o, int l) {
+    if constexpr (G == 1) return o * LS + l;
+    else return (o ^ fold(o >> LG)) * W + l;
+  }
   __device__ __forceinline__ static int fold(int x) {
     if constexpr (G == 2) {
       return __popc(x) & 1;
@@ -837,6 +842,109 @@ __global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<
 }
 
 // ---------------------------------------------------------------------------
+// Row-mode passes (x, contiguous in memory) of real data on the column kernels' register-chained
+// stages, for the periodic and the doubled unbounded cell-centred directions (R2C modes):
+// the CTA's 2W rows are placed as W lanes of packed pairs (row q0 + 2l in the real part, row
+// q0 + 2l + 1 in the imaginary part) in the dense tile the first stage reads, the stages run as in
+// the column kernels, and the modes are split and stored with the lane index fastest, so that
+// a warp touches W lanes of a few consecutive rows of the tile (no bank conflicts) and a few
+// consecutive modes of each of 2W rows in memory (whole sectors).
+// ---------------------------------------------------------------------------
+template <typename T, int PC, int WC, bool HZ, int EPT>
+__global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<T, PC, WC, EPT>::minb)
+    k_fwd_rowx(const __grid_constant__ PassParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int P = PC, W = WC, NT = PC * WC / EPT;
+  using CR = ColRows<T, W>;
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(col_base(smraw));
+  const int tid = threadIdx.x;
+  const int q0 = blockIdx.x * 2 * W;
+  const T* in = (const T*)p.in + (long long)blockIdx.z * p.ai.cs;
+  cpx<T>* out = (cpx<T>*)p.out + (long long)blockIdx.z * p.ao.cs;
+  const int nd = p.n_use;  // P/2 values then zero padding (doubled), or P (periodic)
+  // S[i W + l] = (row q0 + 2l, row q0 + 2l + 1) at position i, lane index fastest: a warp writes
+  // consecutive tile elements and reads a few consecutive values of each of its rows
+  for (int idx = tid; idx < W * nd; idx += NT) {
+    const int l = idx % W, i = idx / W;
+    const int qa = q0 + 2 * l;
+    const T a = qa < p.npen ? in[(long long)qa * p.ai.ls + i] : (T)0;
+    const T b = qa + 1 < p.npen ? in[(long long)(qa + 1) * p.ai.ls + i] : (T)0;
+    S[i * W + l] = mk<T>(a, b);
+  }
+  __syncthreads();
+  ColIO<T> io{};
+  cpx<T> v[EPT];
+  xstages<T, P, W, false, false, 0, XS_NAT, XS_SMEM, HZ, false, EPT>(S, v, (const cpx<T>*)p.tw, tid, io);
+  // modes k = 0 .. P/2 of every lane, split into the two packed rows (Hermitian symmetry)
+  constexpr int NM = P / 2 + 1;
+  for (int idx = tid; idx < W * NM; idx += NT) {
+    const int l = idx % W, k = idx / W;
+    const cpx<T> zk = S[CR::at(k, l)], zm = S[CR::at(k == 0 ? 0 : P - k, l)];
+    const int qa = q0 + 2 * l;
+    if (qa < p.npen) out[(long long)qa * p.ao.ls + k] = split<T>(zk, zm, 0);
+    if (qa + 1 < p.npen) out[(long long)(qa + 1) * p.ao.ls + k] = split<T>(zk, zm, 1);
+  }
+}
+
+template <typename T, int PC, int WC, bool HZ, int EPT>
+__global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<T, PC, WC, EPT>::minb)
+    k_inv_rowx(const __grid_constant__ PassParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int P = PC, W = WC, NT = PC * WC / EPT;
+  using CR = ColRows<T, W>;
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(col_base(smraw));
+  const int tid = threadIdx.x;
+  const int q0 = blockIdx.x * 2 * W;
+  const cpx<T>* in = (const cpx<T>*)p.in + (long long)blockIdx.z * p.ai.cs;
+  T* out = (T*)p.out + (long long)blockIdx.z * p.ao.cs;
+  // with p.rows_bulk the CTA's 2W input rows (contiguous in memory) first arrive by one bulk copy
+  const cpx<T>* rows = in + (long long)q0 * p.ai.ls;
+  if (p.rows_bulk) {
+    unsigned char* sb = smraw + p.rows_off;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(sb) - 16;
+    const int nrows = min(2 * W, p.npen - q0);
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+      const unsigned bytes = (unsigned)((size_t)nrows * p.ai.ls * sizeof(cpx<T>));
+      mbar_expect_tx(bar, bytes);
+      bulk_load(sb, rows, bytes, bar);
+    }
+    const bool ok = mbar_wait_bounded(bar, p.errflag, 2, p.dbg_wait & 2);
+    if (__syncthreads_or(!ok)) return;  // the tile's input did not arrive in time: no stores
+    rows = reinterpret_cast<const cpx<T>*>(sb);
+  }
+  // modes of the two packed rows of every lane -> Z_k = A_k + i B_k and Z_{P-k} = conj(A_k) + i conj(B_k)
+  constexpr int NM = P / 2 + 1;
+  for (int idx = tid; idx < W * NM; idx += NT) {
+    const int l = idx % W, k = idx / W;
+    const int qa = q0 + 2 * l;
+    cpx<T> A = mk<T>((T)0, (T)0), B = A;
+    if (qa < p.npen) A = rows[(long long)(2 * l) * p.ai.ls + k];
+    if (qa + 1 < p.npen) B = rows[(long long)(2 * l + 1) * p.ai.ls + k];
+    if (k == 0 || k == P / 2) {  // DC and Nyquist of a real signal are real
+      A.y = (T)0;
+      B.y = (T)0;
+    }
+    S[k * W + l] = mk<T>(A.x - B.y, A.y + B.x);
+    if (k != 0 && k != P / 2) S[(P - k) * W + l] = mk<T>(A.x + B.y, B.x - A.y);
+  }
+  __syncthreads();
+  ColIO<T> io{};
+  cpx<T> v[EPT];
+  xstages<T, P, W, true, false, 0, XS_NAT, XS_SMEM, false, HZ, EPT>(S, v, (const cpx<T>*)p.tw, tid, io);
+  // data positions i < n_data of both packed rows
+  const int nd = p.n_data;
+  for (int idx = tid; idx < W * nd; idx += NT) {
+    const int l = idx % W, i = idx / W;
+    const cpx<T> z = S[CR::at(i, l)];
+    const int qa = q0 + 2 * l;
+    if (qa < p.npen) out[(long long)qa * p.ao.ls + i] = z.x;
+    if (qa + 1 < p.npen) out[(long long)(qa + 1) * p.ao.ls + i] = z.y;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Instantiation helpers: one launcher and one smem-limit setter per <T, PC, WC>.
 // ---------------------------------------------------------------------------
 // Column kernels with radix-32 stages (32 elements per thread) are compiled for FP32 at P = 1024
@@ -845,6 +953,21 @@ template <typename T, int PC> constexpr bool has_ept32() { return std::is_same<T
 
 template <typename T, int PC, int WC, bool HZ>
 cudaError_t launch_kind_hz(int kind, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st) {
+  if constexpr (PC > 0 && std::is_same<T, float>::value) {
+    if (p.axis == 0 && p.rowx && (kind == K_FWD_REAL || kind == K_INV_REAL)) {
+      const bool fwd = kind == K_FWD_REAL;
+      if constexpr (has_ept32<T, PC>()) {
+        if (p.ept == 32) {
+          if (fwd) k_fwd_rowx<T, PC, WC, HZ, 32><<<grid, nthr, smem, st>>>(p);
+          else k_inv_rowx<T, PC, WC, HZ, 32><<<grid, nthr, smem, st>>>(p);
+          return cudaGetLastError();
+        }
+      }
+      if (fwd) k_fwd_rowx<T, PC, WC, HZ, 16><<<grid, nthr, smem, st>>>(p);
+      else k_inv_rowx<T, PC, WC, HZ, 16><<<grid, nthr, smem, st>>>(p);
+      return cudaGetLastError();
+    }
+  }
   if constexpr (PC > 0) {
     if constexpr (has_ept32<T, PC>()) {
       if (p.axis != 0 && p.ept == 32) {
@@ -900,6 +1023,14 @@ cudaError_t set_limits_hz() {
     if ((e = cudaFuncSetAttribute(k_fwd_c2c_col<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(k_inv_c2c_col<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(k_fused_c2c_col<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if constexpr (std::is_same<T, float>::value) {
+      if ((e = cudaFuncSetAttribute(k_fwd_rowx<T, PC, WC, HZ, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+      if ((e = cudaFuncSetAttribute(k_inv_rowx<T, PC, WC, HZ, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+      if constexpr (has_ept32<T, PC>()) {
+        if ((e = cudaFuncSetAttribute(k_fwd_rowx<T, PC, WC, HZ, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_inv_rowx<T, PC, WC, HZ, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+      }
+    }
     if constexpr (has_ept32<T, PC>()) {
       if ((e = cudaFuncSetAttribute(k_fwd_c2c_col<T, PC, WC, HZ, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
       if ((e = cudaFuncSetAttribute(k_inv_c2c_col<T, PC, WC, HZ, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;

@@ -65,6 +65,7 @@ struct PassParams {
   int hlog;               // log2 of a power of two >= P/2 + 1
   int ct;                 // 1: compile-time tile engine (P = 2^a, W from ct_tile_width)
   int ept;                // column passes of that engine: elements per thread and stage (16 or 32)
+  int rowx;               // x pass of periodic / doubled unbounded real data on the column kernels' stages
   int in_f64, out_f64;    // double-float path: the input / output is the caller's FP64 array
   int hz;                 // cell-centred doubled transform: half-zero input, half output kept (ct engine)
   int gpre;               // fused column pass: copy the tile's stored Green slice to shared memory up front

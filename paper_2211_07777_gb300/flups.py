@@ -422,7 +422,7 @@ class Solver:
             _check(lib().flups_pass_features(self._s, i, ctypes.byref(f)), "flups_pass_features")
             v = f.value
             out.append({"ct": bool(v & 1), "staged_green": bool(v & 2), "tma_green": bool(v & 4), "pruned": bool(v & 8),
-                        "tma_input": bool(v & 16)})
+                        "tma_input": bool(v & 16), "row_stages": bool(v & 32), "bulk_rows": bool(v & 64)})
         return out
 
     def debug_wait_limit(self, mask: int):
