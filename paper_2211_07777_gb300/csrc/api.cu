@@ -114,6 +114,8 @@ struct Launch {
   int user_in, user_out;  // 1: the pointer is the caller's rhs / phi
   int in_buf, out_buf;    // workspace buffer read / written: 1 = W1, 2 = W2, 0 = none
   double bytes, flops;    // algorithmic bytes moved and nominal FFT flops (5 P log2 P per complex FFT)
+  int gnthr;              // x passes on the register-chained stages: the generic row kernel's block
+  size_t gsmem;           // size and shared memory, used when the pass reads or writes pinned host memory
 };
 
 }  // namespace
@@ -816,6 +818,8 @@ void set_rowx(Launch& L, int prec) {
     const int t = (p.ctypes >> (4 * c)) & 15;
     if (!((t == T_UNB && 2 * p.n_data == p.P) || (t == T_PER && p.n_data == p.P))) return;
   }
+  L.gnthr = L.nthr;
+  L.gsmem = L.smem;
   p.rowx = 1;
   // measured at 512^3 (P = 1024): the forward pass runs best with 16 elements per thread (256
   // threads; 0.488 vs 0.516 ms with radix-32 stages), the inverse with radix-32 stages and its
@@ -1204,8 +1208,12 @@ int flups_setup(flups_solver s, void* stream, size_t* workspace_bytes) {
   return FLUPS_OK;
 }
 
-// Launch the whole pass list with the given workspace (W1 at ws, W2 after it).
-static int solve_impl(flups_solver s, void* phi, const void* rhs, void* ws, void* stream) {
+// Launch the whole pass list with the given workspace (W1 at ws, W2 after it).  host_in / host_out:
+// rhs / phi are pinned host memory read or written by the kernels across the host link; the x
+// passes then run the generic row kernels, whose warps touch 128 contiguous bytes of one row (the
+// register-chained ones touch 32-byte pieces of 8 rows, which the link serves less well).
+static int solve_impl(flups_solver s, void* phi, const void* rhs, void* ws, void* stream, bool host_in = false,
+                      bool host_out = false) {
   cudaStream_t st = (cudaStream_t)stream;
   const int prec = s->topo.prec;
   void* W[3] = {nullptr, s->W1, s->W2};
@@ -1229,6 +1237,11 @@ static int solve_impl(flups_solver s, void* phi, const void* rhs, void* ws, void
     if (ws && L.in_buf) {  // the caller's workspace: maps and alignment of its addresses
       encode_input_map(Lw, prec);
       set_rows_bulk(Lw, prec);
+    }
+    if (p.rowx && ((L.user_in && host_in) || (L.user_out && host_out))) {
+      p.rowx = 0;
+      Lw.nthr = L.gnthr;
+      if (!p.rows_bulk) Lw.smem = L.gsmem;
     }
     cudaError_t e = L.kind >= K_CURL_REAL ? launch_curl(L.kind, prec, p, Lw.grid, Lw.nthr, Lw.smem, st)
                                           : launch_pass(L.kind, prec, p, Lw.grid, Lw.nthr, Lw.smem, st);
@@ -1441,7 +1454,7 @@ int flups_solve_host(flups_solver s, void* phi_host, const void* rhs_host, void*
     CK(cudaMemcpyAsync(s->stage, rhs_host, s->user_bytes, cudaMemcpyHostToDevice, st));
     rin = s->stage;
   }
-  int rc = flups_solve(s, rout ? rout : s->stage, rin, stream);
+  int rc = solve_impl(s, rout ? rout : s->stage, rin, nullptr, stream, rin != s->stage, rout != nullptr);
   if (rc) return rc;
   if (!rout) CK(cudaMemcpyAsync(phi_host, s->stage, s->user_bytes, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
