@@ -89,6 +89,14 @@ def workload(name):
                     rhs=lambda: W.periodic_sines((n, n, n), modes), L=(1.0, 1.0, 1.0),
                     rhs_device=lambda dev, dt: W.periodic_sines_torch((n, n, n), modes, dev, dt),
                     check=("sines", modes))
+    if fam.startswith("per") and all(t.isdigit() for t in fam[3:].split("x")) and fam.count("x") == 2:
+        # non-cubic periodic box (small cases of the long transforms for profiling), h = 1/max(n)
+        n = tuple(int(t) for t in fam[3:].split("x"))
+        Lb = tuple(v / max(n) for v in n)
+        modes = W.sine_modes(5)
+        desc = f"fully periodic {n[0]}x{n[1]}x{n[2]} cell-centred {PREC_NAMES[prec]}, spectral kernel"
+        return dict(desc=desc, n=n, bc=((P, P),) * 3, center=W.CELL, prec=prec, kernel="spectral",
+                    rhs=lambda: W.periodic_sines(n, modes, L=1.0), L=Lb, check=None)
     if fam == "mixed257":
         desc = "node-centred 257x256x257, x even-even (DCT-I), y periodic, z unbounded, HEJ2, " \
                f"{PREC_NAMES[prec]}, Gaussian blob sigma=0.08 + 4 seeded y-modes"

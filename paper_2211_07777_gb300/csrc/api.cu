@@ -812,7 +812,7 @@ void encode_input_map(Launch& L, int prec) {
 void set_rowx(Launch& L, int prec) {
   PassParams& p = L.p;
   p.rowx = 0;
-  if (!p.ct || p.axis != 0 || prec != FLUPS_F32 || p.W != 4 || p.center != C_CELL) return;
+  if (!p.ct || p.axis != 0 || (prec != FLUPS_F32 && prec != FLUPS_F64E) || p.W != 4 || p.center != C_CELL) return;
   if (L.kind != K_FWD_REAL && L.kind != K_INV_REAL) return;
   for (int c = 0; c < (int)L.grid.z; ++c) {
     const int t = (p.ctypes >> (4 * c)) & 15;
@@ -824,7 +824,7 @@ void set_rowx(Launch& L, int prec) {
   // measured at 512^3 (P = 1024): the forward pass runs best with 16 elements per thread (256
   // threads; 0.488 vs 0.516 ms with radix-32 stages), the inverse with radix-32 stages and its
   // rows staged by a bulk copy (0.453 ms; 0.492 with 16 elements per thread)
-  p.ept = L.kind == K_FWD_REAL ? 16 : ct_col_ept(p.P, prec, K_FWD_C2C);
+  p.ept = (L.kind == K_FWD_REAL || prec != FLUPS_F32) ? 16 : ct_col_ept(p.P, prec, K_FWD_C2C);
   L.nthr = p.P * p.W / p.ept;
   L.smem = (size_t)p.P * (p.W + 1) * 2 * esize(prec) + 256;
 }

@@ -63,12 +63,17 @@ __device__ __forceinline__ dfloat operator*(dfloat x, dfloat y) {
 
 __device__ __forceinline__ dfloat& operator+=(dfloat& x, dfloat y) { return x = x + y; }
 
-__device__ __forceinline__ dfloat df_from_double(double d) {
-  const float h = __double2float_rn(d);
-  return dfloat(h, __double2float_rn(d - (double)h));
+// Conversions between FP64 and double-float: hi = d rounded to the nearest float, lo = the
+// remainder rounded to the nearest float (hi + lo represents d to 2^-48 relative, |lo| <=
+// ulp(hi)/2); back, the FP64 value nearest to hi + lo.  (Integer-only versions that avoid GB300's
+// FP64 units were measured slower in the double-float x passes: forward 13.9 -> 16.3 ms at
+// 1024^3.)
+__host__ __device__ __forceinline__ dfloat df_from_double(double d) {
+  const float h = (float)d;
+  return dfloat(h, (float)(d - (double)h));
 }
 
-__device__ __forceinline__ double df_to_double(dfloat x) { return (double)x.hi + (double)x.lo; }
+__host__ __device__ __forceinline__ double df_to_double(dfloat x) { return (double)x.hi + (double)x.lo; }
 
 // complex double-float: 16 bytes, laid out like double2 (hi/lo of re, then of im)
 struct __align__(16) cdfloat {

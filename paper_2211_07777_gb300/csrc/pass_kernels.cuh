@@ -863,13 +863,27 @@ __global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<
   cpx<T>* out = (cpx<T>*)p.out + (long long)blockIdx.z * p.ao.cs;
   const int nd = p.n_use;  // P/2 values then zero padding (doubled), or P (periodic)
   // S[i W + l] = (row q0 + 2l, row q0 + 2l + 1) at position i, lane index fastest: a warp writes
-  // consecutive tile elements and reads a few consecutive values of each of its rows
-  for (int idx = tid; idx < W * nd; idx += NT) {
-    const int l = idx % W, i = idx / W;
-    const int qa = q0 + 2 * l;
-    const T a = qa < p.npen ? in[(long long)qa * p.ai.ls + i] : (T)0;
-    const T b = qa + 1 < p.npen ? in[(long long)(qa + 1) * p.ai.ls + i] : (T)0;
-    S[i * W + l] = mk<T>(a, b);
+  // consecutive tile elements and reads a few consecutive values of each of its rows; the loads of
+  // U iterations are issued before any is used: all of a thread's (EPT, or EPT/2 with the zero
+  // half) where the kernel has 128 registers, 8 in the 64-register FP32 kernels
+  constexpr int U = (sizeof(T) > 4 || EPT == 32) ? (HZ ? EPT / 2 : EPT) : 8;
+  const int tot = W * nd;
+  for (int base = tid; base < tot; base += U * NT) {
+    T a[U], b[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * NT;
+      const int l = idx % W, i = idx / W;
+      const int qa = q0 + 2 * l;
+      const long long off = (long long)qa * p.ai.ls + i;
+      a[u] = (idx < tot && qa < p.npen) ? ld_real<T>(in, off, p.in_f64) : (T)0;
+      b[u] = (idx < tot && qa + 1 < p.npen) ? ld_real<T>(in, off + p.ai.ls, p.in_f64) : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * NT;
+      if (idx < tot) S[(idx / W) * W + idx % W] = mk<T>(a[u], b[u]);
+    }
   }
   __syncthreads();
   ColIO<T> io{};
@@ -914,20 +928,35 @@ __global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<
     if (__syncthreads_or(!ok)) return;  // the tile's input did not arrive in time: no stores
     rows = reinterpret_cast<const cpx<T>*>(sb);
   }
-  // modes of the two packed rows of every lane -> Z_k = A_k + i B_k and Z_{P-k} = conj(A_k) + i conj(B_k)
-  constexpr int NM = P / 2 + 1;
-  for (int idx = tid; idx < W * NM; idx += NT) {
-    const int l = idx % W, k = idx / W;
-    const int qa = q0 + 2 * l;
-    cpx<T> A = mk<T>((T)0, (T)0), B = A;
-    if (qa < p.npen) A = rows[(long long)(2 * l) * p.ai.ls + k];
-    if (qa + 1 < p.npen) B = rows[(long long)(2 * l + 1) * p.ai.ls + k];
-    if (k == 0 || k == P / 2) {  // DC and Nyquist of a real signal are real
-      A.y = (T)0;
-      B.y = (T)0;
+  // modes of the two packed rows of every lane -> Z_k = A_k + i B_k and Z_{P-k} = conj(A_k) + i conj(B_k);
+  // the loads of U iterations are issued before any is used
+  constexpr int NM = P / 2 + 1, U = 4;
+  for (int base = tid; base < W * NM; base += U * NT) {
+    cpx<T> A[U], B[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * NT;
+      const int l = idx % W, k = idx / W;
+      const int qa = q0 + 2 * l;
+      A[u] = mk<T>((T)0, (T)0);
+      B[u] = A[u];
+      if (idx < W * NM) {
+        if (qa < p.npen) A[u] = rows[(long long)(2 * l) * p.ai.ls + k];
+        if (qa + 1 < p.npen) B[u] = rows[(long long)(2 * l + 1) * p.ai.ls + k];
+      }
     }
-    S[k * W + l] = mk<T>(A.x - B.y, A.y + B.x);
-    if (k != 0 && k != P / 2) S[(P - k) * W + l] = mk<T>(A.x + B.y, B.x - A.y);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * NT;
+      if (idx >= W * NM) continue;
+      const int l = idx % W, k = idx / W;
+      if (k == 0 || k == P / 2) {  // DC and Nyquist of a real signal are real
+        A[u].y = (T)0;
+        B[u].y = (T)0;
+      }
+      S[k * W + l] = mk<T>(A[u].x - B[u].y, A[u].y + B[u].x);
+      if (k != 0 && k != P / 2) S[(P - k) * W + l] = mk<T>(A[u].x + B[u].y, B[u].x - A[u].y);
+    }
   }
   __syncthreads();
   ColIO<T> io{};
@@ -939,8 +968,9 @@ __global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<
     const int l = idx % W, i = idx / W;
     const cpx<T> z = S[CR::at(i, l)];
     const int qa = q0 + 2 * l;
-    if (qa < p.npen) out[(long long)qa * p.ao.ls + i] = z.x;
-    if (qa + 1 < p.npen) out[(long long)(qa + 1) * p.ao.ls + i] = z.y;
+    const long long off = (long long)qa * p.ao.ls + i;
+    if (qa < p.npen) st_real<T>(out, off, z.x, p.out_f64);
+    if (qa + 1 < p.npen) st_real<T>(out, off + p.ao.ls, z.y, p.out_f64);
   }
 }
 
@@ -953,7 +983,7 @@ template <typename T, int PC> constexpr bool has_ept32() { return std::is_same<T
 
 template <typename T, int PC, int WC, bool HZ>
 cudaError_t launch_kind_hz(int kind, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st) {
-  if constexpr (PC > 0 && std::is_same<T, float>::value) {
+  if constexpr (PC > 0 && (std::is_same<T, float>::value || std::is_same<T, dfloat>::value)) {
     if (p.axis == 0 && p.rowx && (kind == K_FWD_REAL || kind == K_INV_REAL)) {
       const bool fwd = kind == K_FWD_REAL;
       if constexpr (has_ept32<T, PC>()) {
@@ -1023,7 +1053,7 @@ cudaError_t set_limits_hz() {
     if ((e = cudaFuncSetAttribute(k_fwd_c2c_col<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(k_inv_c2c_col<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(k_fused_c2c_col<T, PC, WC, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if constexpr (std::is_same<T, float>::value) {
+    if constexpr (std::is_same<T, float>::value || std::is_same<T, dfloat>::value) {
       if ((e = cudaFuncSetAttribute(k_fwd_rowx<T, PC, WC, HZ, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
       if ((e = cudaFuncSetAttribute(k_inv_rowx<T, PC, WC, HZ, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
       if constexpr (has_ept32<T, PC>()) {
