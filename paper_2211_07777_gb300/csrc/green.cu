@@ -145,17 +145,29 @@ __device__ double hej2_du2(double k, double r, double eps, const GreenSamplePara
     hi = log(50.0 / a);
   }
   // exp(-a e^s - b e^-s) is bounded by 1 in the strip |Im s| < pi/2, so Gauss-Legendre
-  // panels of width 1 (Bernstein ellipse parameter ~6.4) converge like 6.4^-32 with 16 nodes
+  // panels of width 1 (Bernstein ellipse parameter ~6.4) converge like 6.4^-32 with 16 nodes.
+  // At node j of the panel centred at m, e^s = e^m e^{w x_j/2}: the node factors are the same in
+  // every panel of this sample, so each node costs one exponential (of the integrand) instead of
+  // three -- these samples are most of the setup time of plans with two unbounded directions
+  // The nodes come in pairs x_{N-1-j} = -x_j (to the Newton iteration's 1e-16), whose factors
+  // are each other's inverses: 8 factors and their inverses serve all 16 nodes.
   const int npan = max(1, (int)ceil(hi - lo));
   const double w = (hi - lo) / npan;
+  constexpr int H = GL_N / 2;
+  double ef[H], efi[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    ef[j] = exp(0.5 * w * q.gl_x[j]);
+    efi[j] = 1.0 / ef[j];
+  }
   double acc = 0.0;
   for (int pn = 0; pn < npan; ++pn) {
-    const double mid = lo + (pn + 0.5) * w;
+    const double em = exp(lo + (pn + 0.5) * w), emi = 1.0 / em;
+    const double am = a * em, bm = b * emi;
     double pacc = 0.0;
-    for (int j = 0; j < GL_N; ++j) {
-      const double s = mid + 0.5 * w * q.gl_x[j];
-      pacc += q.gl_w[j] * exp(-a * exp(s) - b * exp(-s));
-    }
+#pragma unroll
+    for (int j = 0; j < H; ++j)
+      pacc += q.gl_w[j] * exp(-am * ef[j] - bm * efi[j]) + q.gl_w[GL_N - 1 - j] * exp(-am * efi[j] - bm * ef[j]);
     acc += 0.5 * w * pacc;
   }
   return -acc / (4.0 * PI_D);
@@ -200,7 +212,7 @@ __device__ double hej_higher_order_terms(int m, double k, double r, int du, doub
   return out;
 }
 
-__global__ void k_green_sample(double* __restrict__ g, GreenSampleParams q) {
+__global__ void __launch_bounds__(256, 2) k_green_sample(double* __restrict__ g, GreenSampleParams q) {
   const long long tot = (long long)q.gext[0] * q.gext[1] * q.gext[2];
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
        idx += (long long)gridDim.x * blockDim.x) {
