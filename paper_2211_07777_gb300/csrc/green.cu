@@ -212,6 +212,35 @@ __device__ double hej_higher_order_terms(int m, double k, double r, int du, doub
   return out;
 }
 
+// The kernel's value at spectral wavenumber k and distance r over the unbounded directions.
+__device__ __forceinline__ double green_value(const GreenSampleParams& q, double k, double r) {
+  double v;
+  if (q.kernel == 1) v = hej0_du3(r, q.hmax);
+  else if (q.du == 3) v = hej2_du3(r, q.eps);
+  else if (q.du == 2) v = hej2_du2(k, r, q.eps, q);
+  else v = hej2_du1(k, r, q.eps);
+  if (q.kernel == 0 && q.hej_m > 1) v += hej_higher_order_terms(q.hej_m, k, r, q.du, q.eps);
+  return v;
+}
+
+// Every direction unbounded-like with one spacing h: the kernel is radial and r^2 = h^2 m with
+// m = i^2 + j^2 + k^2, so it is evaluated once per m <= mmax (a table) and gathered -- the padded
+// domains of semi-unbounded directions would otherwise evaluate it at tens of millions of points.
+__global__ void k_green_radial_table(double* __restrict__ t, long long mmax, GreenSampleParams q) {
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m <= mmax; m += (long long)gridDim.x * blockDim.x)
+    t[m] = green_value(q, 0.0, q.h[0] * sqrt((double)m));
+}
+
+__global__ void k_green_radial_gather(double* __restrict__ g, const double* __restrict__ t, GreenSampleParams q) {
+  const long long tot = (long long)q.gext[0] * q.gext[1] * q.gext[2];
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long i = idx % q.gext[0], rest = idx / q.gext[0];
+    const long long j = rest % q.gext[1], k = rest / q.gext[1];
+    g[idx] = t[i * i + j * j + k * k];
+  }
+}
+
 __global__ void __launch_bounds__(256, 2) k_green_sample(double* __restrict__ g, GreenSampleParams q) {
   const long long tot = (long long)q.gext[0] * q.gext[1] * q.gext[2];
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
@@ -231,14 +260,7 @@ __global__ void __launch_bounds__(256, 2) k_green_sample(double* __restrict__ g,
         k2 += w * w;
       }
     }
-    const double k = sqrt(k2), r = sqrt(r2);
-    double v;
-    if (q.kernel == 1) v = hej0_du3(r, q.hmax);
-    else if (q.du == 3) v = hej2_du3(r, q.eps);
-    else if (q.du == 2) v = hej2_du2(k, r, q.eps, q);
-    else v = hej2_du1(k, r, q.eps);
-    if (q.kernel == 0 && q.hej_m > 1) v += hej_higher_order_terms(q.hej_m, k, r, q.du, q.eps);
-    g[idx] = v;
+    g[idx] = green_value(q, sqrt(k2), sqrt(r2));
   }
 }
 
@@ -490,6 +512,25 @@ cudaError_t launch_green_sample(double* g, const GreenSampleParams& q, cudaStrea
   const long long tot = (long long)q.gext[0] * q.gext[1] * q.gext[2];
   long long blocks = (tot + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
+  const bool same_h = fabs(q.h[1] - q.h[0]) <= 1e-13 * q.h[0] && fabs(q.h[2] - q.h[0]) <= 1e-13 * q.h[0];
+  if (q.du == 3 && same_h) {
+    long long mmax = 0;
+    for (int d = 0; d < 3; ++d) mmax += (long long)(q.gext[d] - 1) * (q.gext[d] - 1);
+    if (mmax + 1 < tot) {
+      double* t = nullptr;
+      cudaError_t e = cudaMallocAsync(&t, (size_t)(mmax + 1) * sizeof(double), st);
+      if (e == cudaSuccess) {
+        long long tb = (mmax + 256) / 256;
+        if (tb > 152 * 64) tb = 152 * 64;
+        k_green_radial_table<<<(unsigned)tb, 256, 0, st>>>(t, mmax, q);
+        k_green_radial_gather<<<(unsigned)blocks, 256, 0, st>>>(g, t, q);
+        e = cudaGetLastError();
+        const cudaError_t e2 = cudaFreeAsync(t, st);
+        return e ? e : e2;
+      }
+      cudaGetLastError();  // no room for the table: evaluate every sample
+    }
+  }
   k_green_sample<<<(unsigned)blocks, 256, 0, st>>>(g, q);
   return cudaGetLastError();
 }
