@@ -356,7 +356,9 @@ void fill_geom(Launch& L, const DirPlan& dp, int axis, const int* din, const int
   int wct = share == 1 ? ct_tile_width(dp.P, prec, axis, L.kind) : 0;  // the curl pass keeps the runtime engine
   const int other = axis == 0 ? 1 : (axis == 1 ? din[2] : din[1]);
   auto ctas = [&](int w) { return (long long)((p.npen + (packed ? 2 * w : w) - 1) / (packed ? 2 * w : w)) * other * ncomp; };
-  if (wct && ctas(wct) < 2 * 152) wct = 0;  // small grid: narrower runtime tiles, more CTAs
+  // small grid: narrow compile-time tiles where they are built (FP32, P = 64), else narrower runtime
+  // tiles -- more CTAs either way
+  if (wct && ctas(wct) < 2 * 152) wct = ct_small_width(dp.P, prec);
   if (wct) {
     W = wct;
     nthr = dp.P * W / 16;
@@ -366,9 +368,11 @@ void fill_geom(Launch& L, const DirPlan& dp, int axis, const int* din, const int
     tile_shape(dp.P, prec, p.npen, packed, &W, &nthr, share);
     while (W > 1 && ctas(W) < 2 * 152) W /= 2;
     {
-      int t = (dp.P * W + 15) / 16;
+      // stage engine: 16 elements per thread; warp engine (P <= 32): a column on P lanes
+      const bool wfft = warp_fft_len(dp.P);
+      int t = wfft ? W * dp.P : (dp.P * W + 15) / 16;
       t = ((t + 31) / 32) * 32;
-      nthr = std::min(std::max(t, 64), prec == FLUPS_F32 ? 512 : 256);
+      nthr = std::min(std::max(t, wfft ? 32 : 64), prec == FLUPS_F32 ? 512 : 256);
     }
     p.ct = 0;
     p.LS = (axis == 0 && W >= 8) ? W + 1 : W;
@@ -407,6 +411,7 @@ void fill_geom(Launch& L, const DirPlan& dp, int axis, const int* din, const int
 
 // CTAs per SM the compile-time kernels are built for (their __launch_bounds__ minimum).
 int ct_min_blocks(const PassParams& p, int nthr, int prec) {
+  nthr = std::max(nthr, 32);  // a CTA narrower than a warp holds a whole warp
   if (p.ept == 32) return std::max(1, 512 / nthr);
   return std::max(1, (prec == FLUPS_F32 ? 1024 : 512) / nthr);
 }
@@ -1230,6 +1235,7 @@ static int solve_impl(flups_solver s, void* phi, const void* rhs, void* ws, void
     PassParams& p = Lw.p;
     p.errflag = status;
     p.dbg_wait = s->dbg_wait;
+    p.pdl = 1;  // each pass a programmatic dependent of the stream's previous kernel
     if (L.in_buf) p.in = W[L.in_buf];
     if (L.out_buf) p.out = W[L.out_buf];
     if (L.user_in) p.in = rhs;

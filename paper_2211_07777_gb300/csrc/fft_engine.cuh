@@ -397,6 +397,63 @@ __device__ __forceinline__ cpx<T>* fft_tile(cpx<T>* A, cpx<T>* B, int LS, int P,
 }
 
 // ---------------------------------------------------------------------------
+// Short transforms of the runtime engine (P = 2^a, 4 <= P <= 32): a column is
+// held by P lanes of one warp, lane l keeping element l in a register.
+// Radix-2 decimation in frequency across the lanes: each stage swaps values
+// with lane l ^ h by a warp shuffle, so the stages need neither shared memory
+// nor a block barrier.  Both lanes of a pair run the same instructions (no
+// divergence): the upper lane negates its own value before the sum and
+// multiplies by its twiddle, the lower one by 1.  Lane l ends with mode
+// bitrev(l), written back to the tile in natural order.  The stage engine
+// would give such a column to one or two threads (one or two radix-16
+// butterflies) while the rest of the block waits; on GB300's FP64 units that
+// serial butterfly sets the pass time.  (Longer columns keep the stage
+// engine: its radix-16 butterflies take fewer operations per point than
+// radix-2 stages.)
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T shfl_xor_t(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+template <> __device__ __forceinline__ dfloat shfl_xor_t<dfloat>(dfloat v, int m) {
+  return dfloat(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
+}
+template <typename T> __device__ __forceinline__ cpx<T> shfl_xor_c(cpx<T> v, int m) {
+  return mk<T>(shfl_xor_t<T>(v.x, m), shfl_xor_t<T>(v.y, m));
+}
+
+// Transform the tile in place with the warp engine.  Ends with a block barrier.
+template <typename T, bool INV>
+__device__ __forceinline__ void fft_tile_warp(cpx<T>* S, int LS, int P, int W, const cpx<T>* __restrict__ tw, int tid,
+                                              int nthr) {
+  const int lane = tid & 31, l = lane & (P - 1);
+  const int cpw = 32 / P;                    // columns per warp
+  const int lgP = 31 - __clz(P);
+  const cpx<T> one = mk<T>((T)1, (T)0);
+  // warp-uniform loop: every lane of a warp takes part in its shuffles
+  for (int c0 = (tid >> 5) * cpw; c0 < W; c0 += (nthr >> 5) * cpw) {
+    const int c = c0 + lane / P;
+    const bool ok = c < W;
+    cpx<T> x = ok ? S[l * LS + c] : mk<T>((T)0, (T)0);
+    // span h: lower lane a + b, upper lane (a - b) W_{2h}^{l mod h}, W_{2h}^m = tw[m P / h]
+    for (int h = P >> 1; h >= 1; h >>= 1) {
+      const bool upper = (l & h) != 0;
+      const cpx<T> o = shfl_xor_c<T>(x, h);
+      const cpx<T> y = cadd<T>(upper ? mk<T>(-x.x, -x.y) : x, o);
+      if (h > 1) {
+        const cpx<T> w = upper ? ldg_c<T>(&tw[(l & (h - 1)) * (P / h)]) : one;
+        x = INV ? cmulc<T>(y, w) : cmul<T>(y, w);
+      } else {
+        x = y;
+      }
+    }
+    __syncwarp();  // every lane of the warp has read its element before any is overwritten
+    if (ok) S[(int)(__brev((unsigned)l) >> (32 - lgP)) * LS + c] = x;
+  }
+  __syncthreads();
+}
+
+// the warp engine serves the runtime engine's transforms of these lengths
+__host__ __device__ constexpr bool warp_fft_len(int P) { return P >= 4 && P <= 32 && (P & (P - 1)) == 0; }
+
+// ---------------------------------------------------------------------------
 // Compile-time tile engine for P = 2^a: every stage's radix, stride and
 // twiddle step, the tile width W and the block size NT = P W / 16 are known
 // at compile time, so the index arithmetic folds to shifts and masks.  The

@@ -27,6 +27,16 @@ template <typename T, int WC> __device__ __forceinline__ int tix(int i, int l, i
   else return i * LS + l;
 }
 
+// First statement of every pass kernel.  With p.pdl (programmatic dependent launch, sm_90+), the
+// kernel was launched before the stream's previous kernel completed: wait until that kernel has
+// completed and its writes are visible.  The wait comes before any access to the solve's arrays,
+// so read-after-write and write-after-read order between passes is kept; what overlaps is the
+// launch and CTA start-up of this pass with the exit of the previous one (the dependent launch
+// is triggered as each CTA exits).
+__device__ __forceinline__ void pass_entry(const PassParams& p) {
+  if (p.pdl) asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // Transform type of component `comp` (4 bits per component).
 __device__ __forceinline__ int comp_type(const PassParams& p, int comp) { return (p.ctypes >> (4 * comp)) & 15; }
 

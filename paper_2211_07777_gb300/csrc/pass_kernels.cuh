@@ -27,10 +27,12 @@
 namespace flups {
 
 // Launch bounds: the runtime engine runs at most 512 (FP32) / 256 (FP64)
-// threads; the compile-time engine exactly P W / 16.
+// threads; the compile-time engine exactly P W / 16, and is built for 1024 (FP32) or 512 threads
+// per SM (a CTA narrower than a warp holds a whole warp's registers).
 template <typename T, int PC, int WC> struct KBounds {
   static constexpr int threads = PC ? PC * WC / 16 : (sizeof(T) == 4 ? 512 : 256);
-  static constexpr int minb = PC ? ((sizeof(T) == 4 ? 1024 : 512) / threads > 0 ? (sizeof(T) == 4 ? 1024 : 512) / threads : 1) : 1;
+  static constexpr int wthreads = threads < 32 ? 32 : threads;
+  static constexpr int minb = PC ? ((sizeof(T) == 4 ? 1024 : 512) / wthreads > 0 ? (sizeof(T) == 4 ? 1024 : 512) / wthreads : 1) : 1;
 };
 
 // Column kernels: EPT elements per thread and stage (16, or 32 with radix-32 stages), so
@@ -56,6 +58,10 @@ __device__ __forceinline__ cpx<T>* run_fft(const PassParams& p, cpx<T>* S, cpx<T
     fft_tile_ct<T, PC, WC, INV, ZIN, ZOUT>(S, tw, tid);
     return S;
   } else {
+    if (warp_fft_len(p.P)) {
+      fft_tile_warp<T, INV>(S, p.LS, p.P, p.W, tw, tid, nthr);
+      return S;
+    }
     return fft_tile<T, INV>(S, S2, p.LS, p.P, p.W, p.lw, p.plan, tw, tid, nthr);
   }
 }
@@ -94,6 +100,7 @@ __device__ __forceinline__ cpx<T> stored_mode(const PassParams& p, int type, con
 // ---------------------------------------------------------------------------
 template <typename T, int PC, int WC, bool HZ>
 __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fwd_real(PassParams p) {
+  pass_entry(p);
   extern __shared__ __align__(16) unsigned char smraw[];
   using TL = Tile<T, PC, WC>;
   cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
@@ -163,6 +170,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
 
 template <typename T, int PC, int WC, bool HZ>
 __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_inv_real(PassParams p) {
+  pass_entry(p);
   extern __shared__ __align__(16) unsigned char smraw[];
   using TL = Tile<T, PC, WC>;
   cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
@@ -278,6 +286,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
 // ---------------------------------------------------------------------------
 template <typename T, int PC, int WC, bool HZ>
 __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fwd_c2c(PassParams p) {
+  pass_entry(p);
   extern __shared__ __align__(16) unsigned char smraw[];
   using TL = Tile<T, PC, WC>;
   cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
@@ -303,6 +312,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
 
 template <typename T, int PC, int WC, bool HZ>
 __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_inv_c2c(PassParams p) {
+  pass_entry(p);
   extern __shared__ __align__(16) unsigned char smraw[];
   using TL = Tile<T, PC, WC>;
   cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
@@ -394,6 +404,7 @@ __device__ __forceinline__ size_t tile_bytes(const PassParams& p) {
 
 template <typename T, int PC, int WC, bool HZ>
 __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fused_c2c(PassParams p) {
+  pass_entry(p);
   extern __shared__ __align__(16) unsigned char smraw[];
   using TL = Tile<T, PC, WC>;
   cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
@@ -423,6 +434,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
 
 template <typename T, int PC, int WC, bool HZ>
 __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fused_real(PassParams p) {
+  pass_entry(p);
   extern __shared__ __align__(16) unsigned char smraw[];
   using TL = Tile<T, PC, WC>;
   cpx<T>* S = reinterpret_cast<cpx<T>*>(smraw);
@@ -688,6 +700,7 @@ __device__ __forceinline__ void tile_tma_issue(const PassParams& p, cpx<T>* S, u
 template <typename T, int PC, int WC, bool HZ, int EPT = 16>
 __global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<T, PC, WC, EPT>::minb)
     k_fwd_c2c_col(const __grid_constant__ PassParams p) {
+  pass_entry(p);
   extern __shared__ __align__(16) unsigned char smraw[];
   unsigned char* base = col_base(smraw);
   unsigned long long* mbar_in = reinterpret_cast<unsigned long long*>(base - 128);
@@ -710,6 +723,7 @@ __global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<
 template <typename T, int PC, int WC, bool HZ, int EPT = 16>
 __global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<T, PC, WC, EPT>::minb)
     k_inv_c2c_col(const __grid_constant__ PassParams p) {
+  pass_entry(p);
   extern __shared__ __align__(16) unsigned char smraw[];
   unsigned char* base = col_base(smraw);
   unsigned long long* mbar_in = reinterpret_cast<unsigned long long*>(base - 128);
@@ -733,6 +747,7 @@ __global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<
 template <typename T, int PC, int WC, bool HZ, int EPT = 16>
 __global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<T, PC, WC, EPT>::minb)
     k_fused_c2c_col(const __grid_constant__ PassParams p) {
+  pass_entry(p);
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int P = PC, W = WC, NT = PC * WC / EPT;
   unsigned char* base = col_base(smraw);
@@ -853,6 +868,7 @@ __global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<
 template <typename T, int PC, int WC, bool HZ, int EPT>
 __global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<T, PC, WC, EPT>::minb)
     k_fwd_rowx(const __grid_constant__ PassParams p) {
+  pass_entry(p);
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int P = PC, W = WC, NT = PC * WC / EPT;
   using CR = ColRows<T, W>;
@@ -903,6 +919,7 @@ __global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<
 template <typename T, int PC, int WC, bool HZ, int EPT>
 __global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<T, PC, WC, EPT>::minb)
     k_inv_rowx(const __grid_constant__ PassParams p) {
+  pass_entry(p);
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int P = PC, W = WC, NT = PC * WC / EPT;
   using CR = ColRows<T, W>;
@@ -981,6 +998,22 @@ __global__ void __launch_bounds__(ColBounds<T, PC, WC, EPT>::threads, ColBounds<
 // (the planner uses them for the fused pass).
 template <typename T, int PC> constexpr bool has_ept32() { return std::is_same<T, float>::value && PC == 1024; }
 
+// Launch a pass kernel; with p.pdl as a programmatic dependent of the stream's previous kernel.
+template <typename K>
+cudaError_t pass_launch(K kernel, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3((unsigned)nthr);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = p.pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, p);
+}
+
 template <typename T, int PC, int WC, bool HZ>
 cudaError_t launch_kind_hz(int kind, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st) {
   if constexpr (PC > 0 && (std::is_same<T, float>::value || std::is_same<T, dfloat>::value)) {
@@ -988,13 +1021,13 @@ cudaError_t launch_kind_hz(int kind, const PassParams& p, dim3 grid, int nthr, s
       const bool fwd = kind == K_FWD_REAL;
       if constexpr (has_ept32<T, PC>()) {
         if (p.ept == 32) {
-          if (fwd) k_fwd_rowx<T, PC, WC, HZ, 32><<<grid, nthr, smem, st>>>(p);
-          else k_inv_rowx<T, PC, WC, HZ, 32><<<grid, nthr, smem, st>>>(p);
+          if (fwd) return pass_launch(k_fwd_rowx<T, PC, WC, HZ, 32>, p, grid, nthr, smem, st);
+          else return pass_launch(k_inv_rowx<T, PC, WC, HZ, 32>, p, grid, nthr, smem, st);
           return cudaGetLastError();
         }
       }
-      if (fwd) k_fwd_rowx<T, PC, WC, HZ, 16><<<grid, nthr, smem, st>>>(p);
-      else k_inv_rowx<T, PC, WC, HZ, 16><<<grid, nthr, smem, st>>>(p);
+      if (fwd) return pass_launch(k_fwd_rowx<T, PC, WC, HZ, 16>, p, grid, nthr, smem, st);
+      else return pass_launch(k_inv_rowx<T, PC, WC, HZ, 16>, p, grid, nthr, smem, st);
       return cudaGetLastError();
     }
   }
@@ -1002,32 +1035,31 @@ cudaError_t launch_kind_hz(int kind, const PassParams& p, dim3 grid, int nthr, s
     if constexpr (has_ept32<T, PC>()) {
       if (p.axis != 0 && p.ept == 32) {
         switch (kind) {
-          case K_FWD_C2C: k_fwd_c2c_col<T, PC, WC, HZ, 32><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
-          case K_INV_C2C: k_inv_c2c_col<T, PC, WC, HZ, 32><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
-          case K_FUSED_C2C: k_fused_c2c_col<T, PC, WC, HZ, 32><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
+          case K_FWD_C2C: return pass_launch(k_fwd_c2c_col<T, PC, WC, HZ, 32>, p, grid, nthr, smem, st);
+          case K_INV_C2C: return pass_launch(k_inv_c2c_col<T, PC, WC, HZ, 32>, p, grid, nthr, smem, st);
+          case K_FUSED_C2C: return pass_launch(k_fused_c2c_col<T, PC, WC, HZ, 32>, p, grid, nthr, smem, st);
           default: break;
         }
       }
     }
     if (p.axis != 0) {  // column passes of complex data: register-chained kernels
       switch (kind) {
-        case K_FWD_C2C: k_fwd_c2c_col<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
-        case K_INV_C2C: k_inv_c2c_col<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
-        case K_FUSED_C2C: k_fused_c2c_col<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); return cudaGetLastError();
+        case K_FWD_C2C: return pass_launch(k_fwd_c2c_col<T, PC, WC, HZ>, p, grid, nthr, smem, st);
+        case K_INV_C2C: return pass_launch(k_inv_c2c_col<T, PC, WC, HZ>, p, grid, nthr, smem, st);
+        case K_FUSED_C2C: return pass_launch(k_fused_c2c_col<T, PC, WC, HZ>, p, grid, nthr, smem, st);
         default: break;
       }
     }
   }
   switch (kind) {
-    case K_FWD_REAL: k_fwd_real<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); break;
-    case K_INV_REAL: k_inv_real<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); break;
-    case K_FWD_C2C: k_fwd_c2c<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); break;
-    case K_INV_C2C: k_inv_c2c<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); break;
-    case K_FUSED_REAL: k_fused_real<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); break;
-    case K_FUSED_C2C: k_fused_c2c<T, PC, WC, HZ><<<grid, nthr, smem, st>>>(p); break;
+    case K_FWD_REAL: return pass_launch(k_fwd_real<T, PC, WC, HZ>, p, grid, nthr, smem, st);
+    case K_INV_REAL: return pass_launch(k_inv_real<T, PC, WC, HZ>, p, grid, nthr, smem, st);
+    case K_FWD_C2C: return pass_launch(k_fwd_c2c<T, PC, WC, HZ>, p, grid, nthr, smem, st);
+    case K_INV_C2C: return pass_launch(k_inv_c2c<T, PC, WC, HZ>, p, grid, nthr, smem, st);
+    case K_FUSED_REAL: return pass_launch(k_fused_real<T, PC, WC, HZ>, p, grid, nthr, smem, st);
+    case K_FUSED_C2C: return pass_launch(k_fused_c2c<T, PC, WC, HZ>, p, grid, nthr, smem, st);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 // p.hz: the pass's transform is a cell-centred doubled (unbounded) one -- half of its

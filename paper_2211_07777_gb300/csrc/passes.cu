@@ -36,10 +36,12 @@ cudaError_t set_pass_smem_limits() {
   if (!e) e = set_limits_ct_f32();
   if (!e) e = set_limits_ct_f64();
   if (!e) e = set_limits_ct_df();
+  if (!e) e = set_limits_ct_small();
   return e;
 }
 
 cudaError_t launch_pass(int kind, int prec, const PassParams& p, dim3 grid, int nthr, size_t smem, cudaStream_t st) {
+  if (p.ct && p.W == ct_small_width(p.P, prec)) return launch_ct_small(prec, p.P, kind, p, grid, nthr, smem, st);
   if (prec == 2) return p.ct ? launch_ct_df(p.P, kind, p, grid, nthr, smem, st)
                              : launch_kind<dfloat, 0, 0>(kind, p, grid, nthr, smem, st);
   if (p.ct) return prec == 0 ? launch_ct_f32(p.P, kind, p, grid, nthr, smem, st)

@@ -78,6 +78,8 @@ struct PassParams {
                           // copy into shared memory at byte offset rows_off (after the tile) instead of
                           // per-thread loads
   int rows_off;
+  int pdl;                // launched as a programmatic dependent of the stream's previous kernel: each CTA
+                          // waits for the previous grid (complete, memory visible) before touching memory
   // column passes of the compile-time engine: the input tile by TMA (0 rows: loads from registers)
   int tin_rows;           // rows along the axis copied into the tile (P/2 when pruned, else P)
   int tin_box;            // rows per TMA box
@@ -112,5 +114,10 @@ cudaError_t set_limits_ct_df();
 cudaError_t launch_ct_df_large(int P, int kind, const PassParams& p, dim3 grid, int nthr, size_t smem,
                                cudaStream_t st);
 cudaError_t set_limits_ct_df_large();
+// narrow compile-time tiles for small grids: lanes per tile, 0 when not compiled
+int ct_small_width(int P, int prec);
+cudaError_t launch_ct_small(int prec, int P, int kind, const PassParams& p, dim3 grid, int nthr, size_t smem,
+                            cudaStream_t st);
+cudaError_t set_limits_ct_small();
 
 }  // namespace flups
