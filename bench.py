@@ -489,6 +489,70 @@ def measure_variant(F, torch, name, f_host, ref, flush, stream, K, warmup, peaks
     return rec
 
 
+SMALL_WORKLOADS = ("per32_f64", "per32_f64e", "per32_f32", "unb32_f64", "unb32_f32")
+
+
+def small_record(F, torch, flush, stream, reps=200):
+    """Latency of one small solve (the 32^3 configurations): the solve's five launches captured once
+    in a CUDA graph; each timed replay starts with the L2 flushed (the flush outside the events);
+    median over `reps` replays.  Also the eager launch of the same solve (host launches, L2 flushed)
+    and the back-to-back time per solve of a graph of 32 solves (inputs L2-resident)."""
+    out = {}
+    stream = torch.cuda.Stream(device=stream.device)   # graphs are captured on a non-default stream
+    for name in SMALL_WORKLOADS:
+        wl = workload(name)
+        s = make_solver(F, wl)
+        try:
+            rhs = device_rhs(torch, wl, stream.device)
+            phi = torch.empty_like(rhs)
+            with torch.cuda.stream(stream):
+                s.solve(phi, rhs, stream)
+            torch.cuda.synchronize()
+            rec = {"workload": wl["desc"], "dtype": DTYPES[wl["prec"]]}
+            zidx = sample_planes(wl["n"][2])
+            cf = closed_form_planes(wl, zidx)
+            if cf is not None:
+                rec["rel_err_vs_closed_form"] = rel_linf(phi[zidx].double().cpu().numpy(), cf)
+            g1, g32 = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g1, stream=stream):
+                s.solve(phi, rhs, torch.cuda.current_stream())
+            with torch.cuda.graph(g32, stream=stream):
+                for _ in range(32):
+                    s.solve(phi, rhs, torch.cuda.current_stream())
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            evg = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    g1.replay()
+                    g32.replay()
+                for a, b in ev:         # eager: the solve's launches from the host
+                    flush.zero_()
+                    a.record(stream)
+                    s.solve(phi, rhs, stream)
+                    b.record(stream)
+                for a, b in evg:        # graph replay of one solve
+                    flush.zero_()
+                    a.record(stream)
+                    g1.replay()
+                    b.record(stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(10):
+                    g32.replay()
+                e1.record(stream)
+            torch.cuda.synchronize()
+            rec.update({
+                "graph_us": float(np.median([a.elapsed_time(b) for a, b in evg]) * 1e3),
+                "eager_us": float(np.median([a.elapsed_time(b) for a, b in ev]) * 1e3),
+                "back_to_back_us": float(e0.elapsed_time(e1) / 320 * 1e3),
+                "launches": s.info["launches"], "reps": reps, "device_status": s.check()})
+            out[name] = rec
+            del g1, g32, rhs, phi
+        finally:
+            s.close()
+    return out
+
+
 class L2Flush:
     """Between timed solves: write a buffer twice the L2 size (evicting the solve's data), then read
     another one, so that the next solve starts with no dirty lines of the flush left to write back."""
@@ -649,6 +713,10 @@ def run_ours(args):
             except SystemExit:
                 continue
         line["variants"] = variants
+
+    # small solves (32^3): per-solve latency of graph-replayed and eager launches
+    if rank == 0 and not args.no_variants:
+        line["small"] = small_record(F, torch, flush, stream)
 
     # the served request stream: throughput with p50/p99 latency (rank 0, N = 1)
     if rank == 0 and world == 1 and not args.no_served:

@@ -234,6 +234,10 @@ typedef struct {
   long long submitted, admitted, completed, rejected, failed, queued_max;
   long long plan_hits, plan_misses, slots_created, evictions, plans_cached;
   size_t hbm_in_use, hbm_peak;
+  /* host seconds spent, summed: plan setups on the setup workers (Green spectrum and
+   * twiddles, enqueue to completion), and slot creation on the serving thread (device
+   * arrays and the CUDA graph of the solve) */
+  double setup_seconds, slot_seconds;
 } flups_server_stats;
 
 typedef struct flups_server_s* flups_server;

@@ -450,6 +450,48 @@ __device__ __forceinline__ void fft_tile_warp(cpx<T>* S, int LS, int P, int W, c
   __syncthreads();
 }
 
+// Convolution of a column with the warp engine: forward transform (decimation in frequency,
+// natural order in, lane l ends with mode bitrev(l)), times gain(k) in registers, inverse transform
+// (decimation in time, bit-reversed order in, natural order out) -- no shared-memory round trip and
+// no block barrier between the two transforms.  gain(c, k): the factor of mode k of column c.
+// DIT stage of span h: the upper lane multiplies its value by W_{2h}^{l mod h} (the lower by 1),
+// then lower a + w b, upper a - w b.  Ends with a block barrier.
+template <typename T, typename Gain>
+__device__ __forceinline__ void conv_tile_warp(cpx<T>* S, int LS, int P, int W, const cpx<T>* __restrict__ tw,
+                                               int tid, int nthr, Gain gain) {
+  const int lane = tid & 31, l = lane & (P - 1);
+  const int cpw = 32 / P;
+  const int lgP = 31 - __clz(P);
+  const cpx<T> one = mk<T>((T)1, (T)0);
+  const int kb = (int)(__brev((unsigned)l) >> (32 - lgP));
+  for (int c0 = (tid >> 5) * cpw; c0 < W; c0 += (nthr >> 5) * cpw) {
+    const int c = c0 + lane / P;
+    const bool ok = c < W;
+    cpx<T> x = ok ? S[l * LS + c] : mk<T>((T)0, (T)0);
+    for (int h = P >> 1; h >= 1; h >>= 1) {
+      const bool upper = (l & h) != 0;
+      const cpx<T> o = shfl_xor_c<T>(x, h);
+      const cpx<T> y = cadd<T>(upper ? mk<T>(-x.x, -x.y) : x, o);
+      if (h > 1) {
+        const cpx<T> w = upper ? ldg_c<T>(&tw[(l & (h - 1)) * (P / h)]) : one;
+        x = cmul<T>(y, w);
+      } else {
+        x = y;
+      }
+    }
+    if (ok) x = cscale<T>(x, gain(c, kb));
+    for (int h = 1; h < P; h <<= 1) {
+      const bool upper = (l & h) != 0;
+      const cpx<T> t = (h > 1 && upper) ? cmulc<T>(x, ldg_c<T>(&tw[(l & (h - 1)) * (P / h)])) : x;
+      const cpx<T> o = shfl_xor_c<T>(t, h);
+      x = upper ? csub<T>(o, t) : cadd<T>(t, o);
+    }
+    __syncwarp();
+    if (ok) S[l * LS + c] = x;
+  }
+  __syncthreads();
+}
+
 // the warp engine serves the runtime engine's transforms of these lengths
 __host__ __device__ constexpr bool warp_fft_len(int P) { return P >= 4 && P <= 32 && (P & (P - 1)) == 0; }
 

@@ -22,6 +22,9 @@ template <> __device__ __forceinline__ void st_real<dfloat>(dfloat* a, long long
 
 // Index of element (row i, lane l) of a tile: the compile-time engine's layout (WC > 0) or rows of
 // LS elements (runtime engine).
+// log2 of a power of two, at compile time
+__host__ __device__ constexpr int clog2(int x) { return x <= 1 ? 0 : 1 + clog2(x >> 1); }
+
 template <typename T, int WC> __device__ __forceinline__ int tix(int i, int l, int LS) {
   if constexpr (WC > 0) return CtTile<T, WC>::at(i, l);
   else return i * LS + l;
@@ -131,11 +134,11 @@ __device__ __forceinline__ int primary_pos(int t, int center, int N, int i) {
 // ---------------------------------------------------------------------------
 template <typename T, int WC = 0>
 __device__ __forceinline__ void zero_fill(cpx<T>* S, int LS, int W, int lo, int hi, int tid, int nthr) {
-  // W is a power of two
-  const int tot = (hi - lo) * W;
+  // W is a power of two (index arithmetic by shifts: W is a runtime value in the runtime engine)
+  const int tot = (hi - lo) * W, lw = 31 - __clz(W);
   for (int idx = tid; idx < tot; idx += nthr) {
     const int lane = idx & (W - 1);
-    const int j = lo + idx / W;
+    const int j = lo + (idx >> lw);
     S[tix<T, WC>(j, lane, LS)] = mk<T>((T)0, (T)0);
   }
 }
@@ -145,7 +148,7 @@ __device__ __forceinline__ void zero_fill(cpx<T>* S, int LS, int W, int lo, int 
 template <typename T, int WC = 0>
 __device__ __forceinline__ void load_real_ext(const PassParams& p, int type, const T* __restrict__ in, cpx<T>* S,
                                               int q0, int tid, int nthr, bool skip_zero = false) {
-  const int W = WC ? WC : p.W, LS = WC ? WC + 1 : p.LS, N = p.N, nd = p.n_data;
+  const int W = WC ? WC : p.W, LS = WC ? WC + 1 : p.LS, N = p.N, nd = p.n_data, lw = WC ? clog2(WC) : p.lw;
   const int t = base_type(type);
   const bool rev = is_reversed(type);
   int lo[3], hi[3];
@@ -206,7 +209,7 @@ __device__ __forceinline__ void load_real_ext(const PassParams& p, int type, con
       int c = 0, i = -1;
       if (idx < tot) {
         if (rowmode) { i = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (i >= nd) i = -1; }
-        else { c = idx & (W2 - 1); i = idx / W2; }
+        else { c = idx & (W2 - 1); i = idx >> (lw + 1); }
       }
       cc[u] = c;
       ii[u] = i;
@@ -229,7 +232,7 @@ __device__ __forceinline__ void load_real_ext(const PassParams& p, int type, con
 template <typename T, int WC = 0>
 __device__ __forceinline__ void store_real_data(const PassParams& p, int type, T* __restrict__ out, const cpx<T>* S,
                                                 int q0, int tid, int nthr) {
-  const int W = WC ? WC : p.W, LS = WC ? WC + 1 : p.LS, N = p.N, nd = p.n_data;
+  const int W = WC ? WC : p.W, LS = WC ? WC + 1 : p.LS, N = p.N, nd = p.n_data, lw = WC ? clog2(WC) : p.lw;
   const int t = base_type(type);
   const bool rev = is_reversed(type);
   const int W2 = 2 * W;
@@ -259,7 +262,7 @@ __device__ __forceinline__ void store_real_data(const PassParams& p, int type, T
   for (int idx = tid; idx < tot; idx += nthr) {
     int c, i;
     if (rowmode) { i = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (i >= nd) continue; }
-    else { c = idx & (W2 - 1); i = idx / W2; }
+    else { c = idx & (W2 - 1); i = idx >> (lw + 1); }
     const int q = q0 + c;
     if (q >= p.npen) continue;
     const int ii = rev ? nd - 1 - i : i;
@@ -284,7 +287,7 @@ __device__ __forceinline__ cpx<T> split(cpx<T> zk, cpx<T> zm, int part) {
 template <typename T, int WC = 0>
 __device__ __forceinline__ void load_cplx(const PassParams& p, const cpx<T>* __restrict__ in, cpx<T>* S, int q0,
                                           int tid, int nthr, bool skip_zero = false) {
-  const int W = WC ? WC : p.W, LS = WC ? WC + 1 : p.LS, nu = p.n_use;
+  const int W = WC ? WC : p.W, LS = WC ? WC + 1 : p.LS, nu = p.n_use, lw = WC ? clog2(WC) : p.lw;
   if (nu < p.P && !skip_zero) zero_fill<T, WC>(S, LS, W, nu, p.P, tid, nthr);
   const bool rowmode = p.axis == 0;
   const int tot = rowmode ? (W << p.ndlog) : nu * W;
@@ -298,7 +301,7 @@ __device__ __forceinline__ void load_cplx(const PassParams& p, const cpx<T>* __r
       int lane = 0, i = -1;
       if (idx < tot) {
         if (rowmode) { i = idx & ((1 << p.ndlog) - 1); lane = idx >> p.ndlog; if (i >= nu) i = -1; }
-        else { lane = idx & (W - 1); i = idx / W; }
+        else { lane = idx & (W - 1); i = idx >> lw; }
       }
       ll[u] = lane;
       ii[u] = i;
@@ -314,13 +317,13 @@ __device__ __forceinline__ void load_cplx(const PassParams& p, const cpx<T>* __r
 template <typename T, int WC = 0>
 __device__ __forceinline__ void store_cplx_data(const PassParams& p, cpx<T>* __restrict__ out, const cpx<T>* S, int q0,
                                                 int tid, int nthr) {
-  const int W = WC ? WC : p.W, LS = WC ? WC + 1 : p.LS, nd = p.n_data;
+  const int W = WC ? WC : p.W, LS = WC ? WC + 1 : p.LS, nd = p.n_data, lw = WC ? clog2(WC) : p.lw;
   const bool rowmode = p.axis == 0;
   const int tot = rowmode ? (W << p.ndlog) : nd * W;
   for (int idx = tid; idx < tot; idx += nthr) {
     int lane, i;
     if (rowmode) { i = idx & ((1 << p.ndlog) - 1); lane = idx >> p.ndlog; if (i >= nd) continue; }
-    else { lane = idx & (W - 1); i = idx / W; }
+    else { lane = idx & (W - 1); i = idx >> lw; }
     const int q = q0 + lane;
     if (q >= p.npen) continue;
     const int pos = (p.type == T_PER && p.center == C_NODE && i == p.N) ? 0 : i;

@@ -48,6 +48,7 @@ struct Tile {
   __device__ __forceinline__ static int P(const PassParams& p) { return CT ? PC : p.P; }
   __device__ __forceinline__ static int W(const PassParams& p) { return CT ? WC : p.W; }
   __device__ __forceinline__ static int LS(const PassParams& p) { return CT ? WC + 1 : p.LS; }
+  __device__ __forceinline__ static int lw(const PassParams& p) { return CT ? clog2(WC) : p.lw; }
 };
 
 // FFT of the tile held in S (S2 = second buffer of the runtime engine); returns the buffer holding the result.
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   for (int idx = tid; idx < tot; idx += nthr) {
     int c, k;
     if (rowmode) { k = idx & ((1 << p.ndlog) - 1); c = idx >> p.ndlog; if (k >= nm) continue; }
-    else { c = idx & (W2 - 1); k = idx / W2; }
+    else { c = idx & (W2 - 1); k = idx >> (TL::lw(p) + 1); }
     const int q = q0 + c;
     if (q >= p.npen) continue;
     const int lane = c >> 1, part = c & 1;
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
       int lane = 0, k = -1;
       if (idx < tot) {
         if (rowmode) { k = idx & ((1 << p.hlog) - 1); lane = idx >> p.hlog; if (k > half) k = -1; }
-        else { lane = idx & (W - 1); k = idx / W; }
+        else { lane = idx & (W - 1); k = idx >> TL::lw(p); }
       }
       ll[u] = lane;
       kk[u] = k;
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   const int tot = P * W;
   for (int idx = tid; idx < tot; idx += nthr) {
     int lane, k;
-    if (rowmode) { k = idx % P; lane = idx / P; } else { lane = idx & (W - 1); k = idx / W; }
+    if (rowmode) { k = idx % P; lane = idx / P; } else { lane = idx & (W - 1); k = idx >> TL::lw(p); }
     const int q = q0 + lane;
     if (q >= p.npen) continue;
     out[(long long)q * p.ao.ls + (long long)k * p.ao.js] = S[tix<T, WC>(k, lane, LS)];
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   const int tot = P * W;
   for (int idx = tid; idx < tot; idx += nthr) {
     int lane, k;
-    if (rowmode) { k = idx % P; lane = idx / P; } else { lane = idx & (W - 1); k = idx / W; }
+    if (rowmode) { k = idx % P; lane = idx / P; } else { lane = idx & (W - 1); k = idx >> TL::lw(p); }
     const int q = q0 + lane;
     cpx<T> v = mk<T>((T)0, (T)0);
     if (q < p.npen) v = in[(long long)q * p.ai.ls + (long long)k * p.ai.js];
@@ -419,10 +420,18 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   load_cplx<T, WC>(p, (const cpx<T>*)p.in + obase, S, q0, tid, nthr, HZ);
   __syncthreads();
   const cpx<T>* tw = (const cpx<T>*)p.tw;
+  if constexpr (PC == 0) {
+    if (warp_fft_len(P)) {  // short columns: both transforms and the product in registers
+      conv_tile_warp<T>(S, LS, P, W, tw, tid, nthr,
+                        [&](int c, int k) { return green_at<T>(p, goff[c], k2p[c], min(k, P - k)); });
+      store_cplx_data<T, WC>(p, (cpx<T>*)p.out + obase, S, q0, tid, nthr);
+      return;
+    }
+  }
   cpx<T>* X = run_fft<T, PC, WC, false, HZ, false>(p, S, S2, tw, tid, nthr);
   const int tot = P * W;
   for (int idx = tid; idx < tot; idx += nthr) {
-    const int lane = idx & (W - 1), k = idx / W;
+    const int lane = idx & (W - 1), k = idx >> TL::lw(p);
     const int g3 = min(k, P - k);
     const T G = green_at<T>(p, goff[lane], k2p[lane], g3);
     X[tix<T, WC>(k, lane, LS)] = cscale<T>(X[tix<T, WC>(k, lane, LS)], G);
@@ -455,7 +464,7 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   const int half = P / 2;
   const int tot = (half + 1) * W;
   for (int idx = tid; idx < tot; idx += nthr) {
-    const int lane = idx & (W - 1), k = idx / W;
+    const int lane = idx & (W - 1), k = idx >> TL::lw(p);
     const int km = k == 0 ? 0 : P - k;
     const cpx<T> zk = X[tix<T, WC>(k, lane, LS)], zm = X[tix<T, WC>(km, lane, LS)];
     cpx<T> A = split<T>(zk, zm, 0), B = split<T>(zk, zm, 1);

@@ -9,7 +9,8 @@
 // input/output arrays and the workspace of one solve plus a CUDA graph of the
 // solve's kernel launches, captured once and replayed for every request the
 // slot serves.  New plans are set up by worker threads on their own streams
-// while the serving loop keeps admitting and completing other requests.
+// while the serving loop keeps admitting and completing other requests; the
+// setup queue serves the cheapest setup first within a bounded window.
 // Idle slots and plans are evicted least recently used first when a new
 // request needs the memory.  Completion times come from a host function
 // enqueued after the result's device-to-host copy.  Each slot's workspace
@@ -59,6 +60,7 @@ struct Plan {
   std::vector<Slot*> slots;
   int inflight = 0;
   double last_use = 0;
+  double setup_cost = 0;      // relative cost of the setup (ordering of the setup queue)
   std::atomic<int> state{0};  // 0 building, 1 ready, < 0 setup failed (status)
   bool settled = false;       // transient setup memory returned to the budget
   size_t slot_bytes() const { return 2 * io + ws; }
@@ -126,9 +128,10 @@ struct flups_server_s {
   std::deque<Plan*> builds;
   bool stop = false;
   int building = 0;
+  double setup_seconds = 0;   // guarded by mu
   std::vector<cudaStream_t> streams;
-  cudaStream_t setup_stream = nullptr, capture_stream = nullptr;
   int next_stream = 0;
+  cudaStream_t setup_stream = nullptr, capture_stream = nullptr;
   long long next_ticket = 1;
   std::map<std::string, Plan*> plans;
   std::deque<Pending> queue;
@@ -145,6 +148,8 @@ namespace {
 
 int cu(cudaError_t e) { return e == cudaSuccess ? FLUPS_OK : (e == cudaErrorMemoryAllocation ? FLUPS_ENOMEM : FLUPS_ECUDA); }
 
+constexpr int kBuildWindow = 8;
+
 void worker_main(flups_server_s* sv, int device) {
   cudaSetDevice(device);
   cudaStream_t st = nullptr;
@@ -155,11 +160,23 @@ void worker_main(flups_server_s* sv, int device) {
       std::unique_lock<std::mutex> lk(sv->mu);
       sv->cv.wait(lk, [&] { return sv->stop || !sv->builds.empty(); });
       if (sv->builds.empty()) break;
-      p = sv->builds.front();
-      sv->builds.pop_front();
+      // shortest setup first among the oldest kBuildWindow waiting (bounded reordering: no setup
+      // waits behind more than kBuildWindow - 1 later ones): a small plan's setup takes well under a
+      // millisecond, a large one with a quadrature-sampled Green's function tens of milliseconds
+      auto best = sv->builds.begin();
+      int seen = 0;
+      for (auto it = sv->builds.begin(); it != sv->builds.end() && seen < kBuildWindow; ++it, ++seen)
+        if ((*it)->setup_cost < (*best)->setup_cost) best = it;
+      p = *best;
+      sv->builds.erase(best);
     }
+    const double t0 = now_s();
     const int rc = flups_setup_shared(p->solver, st);
     cudaStreamSynchronize(st);  // every allocation of this setup is complete before anyone frees it
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->setup_seconds += now_s() - t0;
+    }
     p->state.store(rc == FLUPS_OK ? 1 : (rc < 0 ? rc : FLUPS_ECUDA), std::memory_order_release);
   }
   if (st) cudaStreamDestroy(st);
@@ -266,6 +283,11 @@ int new_plan(const flups_request& r, Plan** out) {
   }
   p->io = (size_t)r.n[0] * r.n[1] * r.n[2] * ncomp_of(r) * elem_bytes(r);
   p->key = key_of(r);
+  // setup cost ~ Green samples (the transient FP64 sample array), sampled by quadrature -- several
+  // times dearer per sample -- when exactly two directions are unbounded-like
+  int du = 0;
+  for (int d = 0; d < 3; ++d) du += (r.bc[0][d][0] == FLUPS_UNB || r.bc[0][d][1] == FLUPS_UNB) ? 1 : 0;
+  p->setup_cost = (double)p->transient * (du == 2 ? 8.0 : 1.0) + (double)p->resident;
   *out = p;
   return FLUPS_OK;
 }
@@ -326,6 +348,7 @@ int try_start(flups_server_s* sv, Pending& pd) {
   if (need > sv->budget) return FLUPS_ENOMEM;
   if (!make_room(sv, need, p)) return 0;
   if (!slot) {
+    const double t_slot = now_s();
     slot = new (std::nothrow) Slot;
     if (!slot) return FLUPS_ENOMEM;
     int rc = flups_workspace_status(p->solver, &p->status_off);
@@ -356,6 +379,7 @@ int try_start(flups_server_s* sv, Pending& pd) {
     }
     p->slots.push_back(slot);
     sv->st.slots_created++;
+    sv->st.slot_seconds += now_s() - t_slot;
   }
   if (sv->in_use > sv->peak) sv->peak = sv->in_use;
   cudaStream_t s = sv->streams[sv->next_stream];
@@ -549,6 +573,8 @@ int flups_server_get_stats(flups_server sv, flups_server_stats* out) {
   out->hbm_in_use = sv->in_use;
   out->hbm_peak = sv->peak;
   out->plans_cached = (long long)sv->plans.size();
+  std::lock_guard<std::mutex> lk(sv->mu);
+  out->setup_seconds = sv->setup_seconds;
   return FLUPS_OK;
 }
 

@@ -45,7 +45,8 @@ class ServerStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_longlong) for k in ("submitted", "admitted", "completed", "rejected", "failed",
                                                    "queued_max", "plan_hits", "plan_misses", "slots_created",
                                                    "evictions", "plans_cached")] + \
-               [("hbm_in_use", ctypes.c_size_t), ("hbm_peak", ctypes.c_size_t)]
+               [("hbm_in_use", ctypes.c_size_t), ("hbm_peak", ctypes.c_size_t)] + \
+               [("setup_seconds", ctypes.c_double), ("slot_seconds", ctypes.c_double)]
 
 
 class FlupsError(RuntimeError):

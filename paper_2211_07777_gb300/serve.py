@@ -79,12 +79,13 @@ class HostPool:
 
 
 def run_stream(reqs, budget_bytes, nstreams=8, time_scale=1.0, closed_loop=False, keep=None, pool=None,
-               fp64_engine="native"):
+               fp64_engine="native", per_request=False):
     """Submit reqs (sorted by arrival) and collect completions.
 
     time_scale multiplies the arrival times (open loop); closed_loop submits all at once.
     keep: set of request ids whose outputs are copied out and returned.
     fp64_engine: "native" or "df" (see engine_prec).
+    per_request: also return 'latency_s', the latency of every completed request by id.
     Returns a summary dict (+ 'outputs' for the kept ids)."""
     pool = pool or HostPool()
     for r in reqs:
@@ -146,4 +147,6 @@ def run_stream(reqs, budget_bytes, nstreams=8, time_scale=1.0, closed_loop=False
                              "mpts": sum(pts[r.rid] for r in reqs if r.rid in lat and r.prec == prec) / 1e6}
     if keep is not None:
         summary["outputs"] = outputs
+    if per_request:
+        summary["latency_s"] = dict(lat)
     return summary
