@@ -349,7 +349,8 @@ def traffic_record(kernel_name, workload_name):
 # the sources that define the compile-time pass kernels (the FFT engine, the tile loaders, the
 # pass kernels and their instantiations); the host planner and the other kernels are not among them
 KERNEL_SOURCES = ("fft_engine.cuh", "dfloat.cuh", "passes.cuh", "pass_common.cuh", "pass_kernels.cuh",
-                  "passes_ct_f32.cu", "passes_ct_f64.cu", "passes_ct_df.cu", "passes_ct_df_large.cu")
+                  "passes_ct_f32.cu", "passes_ct_f64.cu", "passes_ct_df.cu", "passes_ct_df_large.cu",
+                  "passes_ct_small.cu")
 
 
 def kernel_source_sha():
