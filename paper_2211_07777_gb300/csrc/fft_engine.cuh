@@ -419,13 +419,15 @@ template <typename T> __device__ __forceinline__ cpx<T> shfl_xor_c(cpx<T> v, int
   return mk<T>(shfl_xor_t<T>(v.x, m), shfl_xor_t<T>(v.y, m));
 }
 
-// Transform the tile in place with the warp engine.  Ends with a block barrier.
-template <typename T, bool INV>
-__device__ __forceinline__ void fft_tile_warp(cpx<T>* S, int LS, int P, int W, const cpx<T>* __restrict__ tw, int tid,
-                                              int nthr) {
+// Transform the tile's columns with the warp engine; out(c, k, v) receives mode k of column c from the
+// lane that holds it (after every lane of the warp has read its element of the tile).
+template <typename T, bool INV, typename Out>
+__device__ __forceinline__ void fft_cols_warp(const cpx<T>* S, int LS, int P, int W, const cpx<T>* __restrict__ tw,
+                                              int tid, int nthr, Out out) {
   const int lane = tid & 31, l = lane & (P - 1);
   const int cpw = 32 / P;                    // columns per warp
   const int lgP = 31 - __clz(P);
+  const int kb = (int)(__brev((unsigned)l) >> (32 - lgP));
   const cpx<T> one = mk<T>((T)1, (T)0);
   // warp-uniform loop: every lane of a warp takes part in its shuffles
   for (int c0 = (tid >> 5) * cpw; c0 < W; c0 += (nthr >> 5) * cpw) {
@@ -445,20 +447,27 @@ __device__ __forceinline__ void fft_tile_warp(cpx<T>* S, int LS, int P, int W, c
       }
     }
     __syncwarp();  // every lane of the warp has read its element before any is overwritten
-    if (ok) S[(int)(__brev((unsigned)l) >> (32 - lgP)) * LS + c] = x;
+    if (ok) out(c, kb, x);
   }
+}
+
+// Transform the tile in place with the warp engine.  Ends with a block barrier.
+template <typename T, bool INV>
+__device__ __forceinline__ void fft_tile_warp(cpx<T>* S, int LS, int P, int W, const cpx<T>* __restrict__ tw, int tid,
+                                              int nthr) {
+  fft_cols_warp<T, INV>(S, LS, P, W, tw, tid, nthr, [&](int c, int k, const cpx<T>& v) { S[k * LS + c] = v; });
   __syncthreads();
 }
 
 // Convolution of a column with the warp engine: forward transform (decimation in frequency,
-// natural order in, lane l ends with mode bitrev(l)), times gain(k) in registers, inverse transform
-// (decimation in time, bit-reversed order in, natural order out) -- no shared-memory round trip and
-// no block barrier between the two transforms.  gain(c, k): the factor of mode k of column c.
-// DIT stage of span h: the upper lane multiplies its value by W_{2h}^{l mod h} (the lower by 1),
-// then lower a + w b, upper a - w b.  Ends with a block barrier.
-template <typename T, typename Gain>
-__device__ __forceinline__ void conv_tile_warp(cpx<T>* S, int LS, int P, int W, const cpx<T>* __restrict__ tw,
-                                               int tid, int nthr, Gain gain) {
+// natural order in, lane l ends with mode bitrev(l)), times gain(c, k) in registers, inverse
+// transform (decimation in time, bit-reversed order in, natural order out) -- no shared-memory round
+// trip and no block barrier between the two transforms.  out(c, i, v) receives position i of column
+// c from lane i.  DIT stage of span h: the upper lane multiplies its value by W_{2h}^{l mod h} (the
+// lower by 1), then lower a + w b, upper a - w b.
+template <typename T, typename Gain, typename Out>
+__device__ __forceinline__ void conv_cols_warp(const cpx<T>* S, int LS, int P, int W, const cpx<T>* __restrict__ tw,
+                                               int tid, int nthr, Gain gain, Out out) {
   const int lane = tid & 31, l = lane & (P - 1);
   const int cpw = 32 / P;
   const int lgP = 31 - __clz(P);
@@ -486,10 +495,8 @@ __device__ __forceinline__ void conv_tile_warp(cpx<T>* S, int LS, int P, int W, 
       const cpx<T> o = shfl_xor_c<T>(t, h);
       x = upper ? csub<T>(o, t) : cadd<T>(t, o);
     }
-    __syncwarp();
-    if (ok) S[l * LS + c] = x;
+    if (ok) out(c, l, x);
   }
-  __syncthreads();
 }
 
 // the warp engine serves the runtime engine's transforms of these lengths

@@ -285,6 +285,17 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
 // ---------------------------------------------------------------------------
 // Complex passes (second and third complex directions).
 // ---------------------------------------------------------------------------
+
+// Store of an inverse complex pass from the lane holding extension position i of pencil q (the
+// element-wise form of store_cplx_data): data index i < n_data, and node-centred periodic
+// phi_N := phi_0.
+template <typename T>
+__device__ __forceinline__ void store_cplx_at(const PassParams& p, cpx<T>* out, int q, int i, const cpx<T>& v) {
+  if (q >= p.npen) return;
+  const long long row = (long long)q * p.ao.ls;
+  if (i < p.n_data) out[row + (long long)i * p.ao.js] = v;
+  if (i == 0 && p.type == T_PER && p.center == C_NODE && p.N < p.n_data) out[row + (long long)p.N * p.ao.js] = v;
+}
 template <typename T, int PC, int WC, bool HZ>
 __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC>::minb) k_fwd_c2c(PassParams p) {
   pass_entry(p);
@@ -298,8 +309,17 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   const long long obase_o = (long long)blockIdx.y * p.ao.os + (long long)blockIdx.z * p.ao.cs;
   load_cplx<T, WC>(p, (const cpx<T>*)p.in + obase_i, S, q0, tid, nthr, HZ);
   __syncthreads();
-  S = run_fft<T, PC, WC, false, HZ, false>(p, S, second_buffer<T, PC>(p, S), (const cpx<T>*)p.tw, tid, nthr);
   cpx<T>* out = (cpx<T>*)p.out + obase_o;
+  if constexpr (PC == 0) {
+    if (warp_fft_len(P)) {  // short columns: modes stored from the lanes' registers
+      fft_cols_warp<T, false>(S, LS, P, W, (const cpx<T>*)p.tw, tid, nthr, [&](int c, int k, const cpx<T>& v) {
+        const int q = q0 + c;
+        if (q < p.npen) out[(long long)q * p.ao.ls + (long long)k * p.ao.js] = v;
+      });
+      return;
+    }
+  }
+  S = run_fft<T, PC, WC, false, HZ, false>(p, S, second_buffer<T, PC>(p, S), (const cpx<T>*)p.tw, tid, nthr);
   const bool rowmode = p.axis == 0;
   const int tot = P * W;
   for (int idx = tid; idx < tot; idx += nthr) {
@@ -334,6 +354,14 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     S[tix<T, WC>(k, lane, LS)] = v;
   }
   __syncthreads();
+  if constexpr (PC == 0) {
+    if (warp_fft_len(P)) {  // short columns: data stored from the lanes' registers
+      cpx<T>* out = (cpx<T>*)p.out + obase_o;
+      fft_cols_warp<T, true>(S, LS, P, W, (const cpx<T>*)p.tw, tid, nthr,
+                             [&](int c, int k, const cpx<T>& v) { store_cplx_at<T>(p, out, q0 + c, k, v); });
+      return;
+    }
+  }
   S = run_fft<T, PC, WC, true, false, HZ>(p, S, second_buffer<T, PC>(p, S), (const cpx<T>*)p.tw, tid, nthr);
   store_cplx_data<T, WC>(p, (cpx<T>*)p.out + obase_o, S, q0, tid, nthr);
 }
@@ -421,10 +449,11 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   __syncthreads();
   const cpx<T>* tw = (const cpx<T>*)p.tw;
   if constexpr (PC == 0) {
-    if (warp_fft_len(P)) {  // short columns: both transforms and the product in registers
-      conv_tile_warp<T>(S, LS, P, W, tw, tid, nthr,
-                        [&](int c, int k) { return green_at<T>(p, goff[c], k2p[c], min(k, P - k)); });
-      store_cplx_data<T, WC>(p, (cpx<T>*)p.out + obase, S, q0, tid, nthr);
+    if (warp_fft_len(P)) {  // short columns: both transforms, the product and the store from registers
+      cpx<T>* out = (cpx<T>*)p.out + obase;
+      conv_cols_warp<T>(S, LS, P, W, tw, tid, nthr,
+                        [&](int c, int k) { return green_at<T>(p, goff[c], k2p[c], min(k, P - k)); },
+                        [&](int c, int i, const cpx<T>& v) { store_cplx_at<T>(p, out, q0 + c, i, v); });
       return;
     }
   }
