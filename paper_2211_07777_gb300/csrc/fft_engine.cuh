@@ -418,9 +418,18 @@ template <> __device__ __forceinline__ dfloat shfl_xor_t<dfloat>(dfloat v, int m
 template <typename T> __device__ __forceinline__ cpx<T> shfl_xor_c(cpx<T> v, int m) {
   return mk<T>(shfl_xor_t<T>(v.x, m), shfl_xor_t<T>(v.y, m));
 }
+template <typename T> __device__ __forceinline__ T shfl_idx_t(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+template <> __device__ __forceinline__ dfloat shfl_idx_t<dfloat>(dfloat v, int src) {
+  return dfloat(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+}
+template <typename T> __device__ __forceinline__ cpx<T> shfl_idx_c(cpx<T> v, int src) {
+  return mk<T>(shfl_idx_t<T>(v.x, src), shfl_idx_t<T>(v.y, src));
+}
 
-// Transform the tile's columns with the warp engine; out(c, k, v) receives mode k of column c from the
-// lane that holds it (after every lane of the warp has read its element of the tile).
+// Transform the tile's columns with the warp engine; out(c, k, v, ok) receives mode k of column c from
+// the lane that holds it (after every lane of the warp has read its element of the tile).  Every
+// lane of the warp calls it, so it may exchange values between lanes; ok is false on lanes past the
+// tile's last column, whose v is not a mode.
 template <typename T, bool INV, typename Out>
 __device__ __forceinline__ void fft_cols_warp(const cpx<T>* S, int LS, int P, int W, const cpx<T>* __restrict__ tw,
                                               int tid, int nthr, Out out) {
@@ -447,7 +456,7 @@ __device__ __forceinline__ void fft_cols_warp(const cpx<T>* S, int LS, int P, in
       }
     }
     __syncwarp();  // every lane of the warp has read its element before any is overwritten
-    if (ok) out(c, kb, x);
+    out(c, kb, x, ok);
   }
 }
 
@@ -455,7 +464,9 @@ __device__ __forceinline__ void fft_cols_warp(const cpx<T>* S, int LS, int P, in
 template <typename T, bool INV>
 __device__ __forceinline__ void fft_tile_warp(cpx<T>* S, int LS, int P, int W, const cpx<T>* __restrict__ tw, int tid,
                                               int nthr) {
-  fft_cols_warp<T, INV>(S, LS, P, W, tw, tid, nthr, [&](int c, int k, const cpx<T>& v) { S[k * LS + c] = v; });
+  fft_cols_warp<T, INV>(S, LS, P, W, tw, tid, nthr, [&](int c, int k, const cpx<T>& v, bool ok) {
+    if (ok) S[k * LS + c] = v;
+  });
   __syncthreads();
 }
 

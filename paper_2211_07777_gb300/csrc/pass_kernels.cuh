@@ -114,7 +114,6 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   load_real_ext<T, WC>(p, ctype, (const T*)p.in + obase_i, S, q0, tid, nthr, HZ);
   __syncthreads();
   const cpx<T>* tw = (const cpx<T>*)p.tw;
-  S = run_fft<T, PC, WC, false, HZ, false>(p, S, second_buffer<T, PC>(p, S), tw, tid, nthr);
 
   const int t = base_type(ctype);
   const bool cplx_out = (t == T_PER || t == T_UNB);
@@ -135,6 +134,27 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
       st_real<T>((T*)p.out, obase_o + off, v, p.out_f64);
     }
   };
+  if constexpr (PC == 0) {
+    if (warp_fft_len(P)) {
+      // short columns: the lane holding mode kk takes the mirrored mode P - kk from the lane that
+      // holds it, separates the two packed pencils and stores both coefficients from registers
+      const int lgP = 31 - __clz(P);
+      fft_cols_warp<T, false>(S, LS, P, W, tw, tid, nthr, [&](int c, int kk, const cpx<T>& zk, bool ok) {
+        const int km = kk == 0 ? 0 : P - kk;
+        const int src = ((tid & 31) & ~(P - 1)) | (int)(__brev((unsigned)km) >> (32 - lgP));
+        const cpx<T> zm = shfl_idx_c<T>(zk, src);
+        if (!ok || (quarter && !(kk & 1))) return;
+        const int k = quarter ? (kk - 1) >> 1 : kk;
+        if (k >= nm) return;
+        for (int part = 0; part < 2; ++part) {
+          const int q = q0 + 2 * c + part;
+          if (q < p.npen) store_mode(q, k, kk, split<T>(zk, zm, part));
+        }
+      });
+      return;
+    }
+  }
+  S = run_fft<T, PC, WC, false, HZ, false>(p, S, second_buffer<T, PC>(p, S), tw, tid, nthr);
   if (PC > 0 && rowmode) {
     // compile-time tile in row mode: a thread reads Z_k and Z_{P-k} of a lane once and stores the
     // mode of both of its pencils; modes k < P/2 as W rows of P/2 (8 per thread, k fastest), then
@@ -278,6 +298,23 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
     }
   }
   __syncthreads();
+  if constexpr (PC == 0) {
+    if (warp_fft_len(P) && p.center == C_CELL) {
+      // short columns of cell-centred data (data index = extension position, or its reversal): the
+      // lane holding position pos stores that value of both packed pencils from registers
+      const bool rev = is_reversed(ctype);
+      const int nd = p.n_data;
+      T* out = (T*)p.out + obase_o;
+      fft_cols_warp<T, true>(S, LS, P, W, tw, tid, nthr, [&](int c, int pos, const cpx<T>& z, bool ok) {
+        if (!ok || pos >= nd) return;
+        const long long off = (long long)(rev ? nd - 1 - pos : pos) * p.ao.js;
+        const int qa = q0 + 2 * c;
+        if (qa < p.npen) st_real<T>(out, (long long)qa * p.ao.ls + off, z.x, p.out_f64);
+        if (qa + 1 < p.npen) st_real<T>(out, (long long)(qa + 1) * p.ao.ls + off, z.y, p.out_f64);
+      });
+      return;
+    }
+  }
   S = run_fft<T, PC, WC, true, false, HZ>(p, S, second_buffer<T, PC>(p, S), tw, tid, nthr);
   store_real_data<T, WC>(p, ctype, (T*)p.out + obase_o, S, q0, tid, nthr);
 }
@@ -312,10 +349,11 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   cpx<T>* out = (cpx<T>*)p.out + obase_o;
   if constexpr (PC == 0) {
     if (warp_fft_len(P)) {  // short columns: modes stored from the lanes' registers
-      fft_cols_warp<T, false>(S, LS, P, W, (const cpx<T>*)p.tw, tid, nthr, [&](int c, int k, const cpx<T>& v) {
-        const int q = q0 + c;
-        if (q < p.npen) out[(long long)q * p.ao.ls + (long long)k * p.ao.js] = v;
-      });
+      fft_cols_warp<T, false>(S, LS, P, W, (const cpx<T>*)p.tw, tid, nthr,
+                              [&](int c, int k, const cpx<T>& v, bool ok) {
+                                const int q = q0 + c;
+                                if (ok && q < p.npen) out[(long long)q * p.ao.ls + (long long)k * p.ao.js] = v;
+                              });
       return;
     }
   }
@@ -357,8 +395,9 @@ __global__ void __launch_bounds__(KBounds<T, PC, WC>::threads, KBounds<T, PC, WC
   if constexpr (PC == 0) {
     if (warp_fft_len(P)) {  // short columns: data stored from the lanes' registers
       cpx<T>* out = (cpx<T>*)p.out + obase_o;
-      fft_cols_warp<T, true>(S, LS, P, W, (const cpx<T>*)p.tw, tid, nthr,
-                             [&](int c, int k, const cpx<T>& v) { store_cplx_at<T>(p, out, q0 + c, k, v); });
+      fft_cols_warp<T, true>(S, LS, P, W, (const cpx<T>*)p.tw, tid, nthr, [&](int c, int k, const cpx<T>& v, bool ok) {
+        if (ok) store_cplx_at<T>(p, out, q0 + c, k, v);
+      });
       return;
     }
   }
