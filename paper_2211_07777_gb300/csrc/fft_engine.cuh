@@ -404,7 +404,8 @@ __device__ __forceinline__ cpx<T>* fft_tile(cpx<T>* A, cpx<T>* B, int LS, int P,
 // nor a block barrier.  Both lanes of a pair run the same instructions (no
 // divergence): the upper lane negates its own value before the sum and
 // multiplies by its twiddle, the lower one by 1.  Lane l ends with mode
-// bitrev(l), written back to the tile in natural order.  The stage engine
+// bitrev(l), which the caller writes back to the tile in natural order or
+// stores from the register.  Block sizes are whole warps.  The stage engine
 // would give such a column to one or two threads (one or two radix-16
 // butterflies) while the rest of the block waits; on GB300's FP64 units that
 // serial butterfly sets the pass time.  (Longer columns keep the stage
