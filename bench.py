@@ -396,6 +396,16 @@ def make_solver(F, wl):
                     h=wl.get("h"))
 
 
+def timed_setup(F, torch, wl):
+    """A solver of the workload and its setup time in ms: plan, twiddles and Green spectrum, host and
+    device, synchronised on both sides.  The solve rates exclude it; the lines report it beside them."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = make_solver(F, wl)
+    torch.cuda.synchronize()
+    return s, (time.perf_counter() - t0) * 1e3
+
+
 def device_rhs(torch, wl, dev, f_host=None):
     dt = torch.float32 if wl["prec"] == 0 else torch.float64
     if f_host is None and "rhs_device" in wl:
@@ -460,13 +470,13 @@ def measure_variant(F, torch, name, f_host, ref, flush, stream, K, warmup, peaks
     """Time another workload or arithmetic path (whole solves, per-pass events, L2 flushed); its
     error against `ref` (the oracle's field of the same input) or against the closed form."""
     wl = workload(name)
-    s = make_solver(F, wl)
+    s, setup_ms = timed_setup(F, torch, wl)
     try:
         rhs = device_rhs(torch, wl, stream.device, f_host)
         phi = torch.empty_like(rhs)
         s.solve(phi, rhs, stream)
         torch.cuda.synchronize()
-        rec = {"dtype": DTYPES[wl["prec"]], "workload": wl["desc"]}
+        rec = {"dtype": DTYPES[wl["prec"]], "workload": wl["desc"], "setup_ms": setup_ms}
         if ref is not None:
             rec["max_rel_err_vs_oracle"] = rel_linf(phi.double().cpu().numpy(), ref)
         zidx = sample_planes(wl["n"][2])
@@ -502,14 +512,14 @@ def small_record(F, torch, flush, stream, reps=200):
     stream = torch.cuda.Stream(device=stream.device)   # graphs are captured on a non-default stream
     for name in SMALL_WORKLOADS:
         wl = workload(name)
-        s = make_solver(F, wl)
+        s, setup_ms = timed_setup(F, torch, wl)
         try:
             rhs = device_rhs(torch, wl, stream.device)
             phi = torch.empty_like(rhs)
             with torch.cuda.stream(stream):
                 s.solve(phi, rhs, stream)
             torch.cuda.synchronize()
-            rec = {"workload": wl["desc"], "dtype": DTYPES[wl["prec"]]}
+            rec = {"workload": wl["desc"], "dtype": DTYPES[wl["prec"]], "setup_ms": setup_ms}
             zidx = sample_planes(wl["n"][2])
             cf = closed_form_planes(wl, zidx)
             if cf is not None:
@@ -612,7 +622,7 @@ def run_ours(args):
     f_host = wl["rhs"]()
     pts = float(np.prod(wl["n"]))
     peaks = fma_peaks(F) if rank == 0 else {}
-    solver = make_solver(F, wl)
+    solver, setup_ms = timed_setup(F, torch, wl)
     rhs = device_rhs(torch, wl, dev, f_host)
     phi = torch.empty_like(rhs)
     stream = torch.cuda.current_stream(dev)
@@ -683,6 +693,7 @@ def run_ours(args):
         "clocks": clk.summary(),
         "device_status": device_status,
         "peaks": peaks,
+        "setup_ms": setup_ms,
     }
     if cf is not None:
         line["rel_err_vs_closed_form"] = rel_linf(got[zidx], cf)
