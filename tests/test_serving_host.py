@@ -33,3 +33,21 @@ def test_vector_bc_wall_rule_is_consistent_for_the_curl():
                 t1 = tuple(sw(x) for x in f[b][d]) if d == a else f[b][d]
                 t2 = tuple(sw(x) for x in f[a][d]) if d == b else f[a][d]
                 assert t1 == t2
+
+
+def test_request_marshalling_and_fp64_engine_policy():
+    """A served request becomes the C request the server plans from: the precision follows the FP64
+    engine policy, Biot-Savart requests carry the wall-rule conditions of all three components, the
+    spacing is L / n (cell-centred) and the kernel is the stream's."""
+    from paper_2211_07777_gb300 import flups as F
+    reqs = W.served_stream(nreq=200, seed=4)
+    for r in reqs[:60]:
+        for eng in ("native", "df"):
+            c = serve.c_request(r, eng)
+            want = F.F64E if (eng == "df" and r.prec == F.F64) else r.prec
+            assert c.prec == want and serve.engine_prec(r, eng) == want
+            assert list(c.n) == list(r.n) and c.op == r.op and c.green == r.kernel and c.center == F.CELL
+            assert list(c.h) == [1.0 / r.n[d] for d in range(3)]
+            bc = serve.vector_bc(r.bc) if r.op == F.BIOT_SAVART else (r.bc,)
+            flat = [b for comp in bc for d in comp for b in d]
+            assert list(c.bc)[:len(flat)] == flat and all(v == 0 for v in list(c.bc)[len(flat):])
